@@ -1,0 +1,463 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by the mathematics (CPU only).
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term, a wrong sign or
+index, a transposed operand) fails it:
+  * exact relativistic Riemann solution of the Sod tube of §5.1 (closed form + root solve);
+  * discrete conservation in a periodic Minkowski box (§2.1 Eq. 2 is in conservation form);
+  * conservation of D, T_t and B in a static curved periodic metric (S_t = 0 when d_t g = 0);
+  * recovery round trip w(u(w)) = w (§2.2: u(w) is the inverse of the algebraic w(u));
+  * four-vector identities u.u = -1, b.u = 0, T^{mu nu} u_mu u_nu = w - p + b^2/2;
+  * the source identity T^k_l Gamma^l_{mu k} = 1/2 T^{kl} d_mu g_{kl} with Christoffels
+    computed here from the metric derivatives;
+  * closed-form wave speeds (at rest: +-c_ms; boosted sound: relativistic velocity addition);
+  * the induction sign (a tangential field advected by a uniform flow moves with it);
+  * B^x of a 1-D magnetised tube stays exactly constant, uniform states stay exactly uniform;
+  * x/y/z symmetry of a tube, second-order spatial and third-order temporal convergence.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from exact_riemann import RiemannSolution
+from paper_1102_5202_gb300 import workloads as W
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def _setup(P, **kw):
+    grid = O.make_grid(P.n, P.dx, P.bc)
+    opts = O.make_opts(P.gamma, cleaning=P.cleaning, ch=P.ch, kappa=P.kappa,
+                       rho_floor=P.rho_floor, p_floor=P.p_floor, atm_K=P.atm_K, **kw)
+    return grid, opts
+
+
+def _read_golden(name):
+    rows = []
+    with open(f"{GOLDEN}/{name}") as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------------- exact Riemann
+def test_exact_solver_matches_published_star_state():
+    sol = RiemannSolution(5.0 / 3.0, (10.0, 13.33, 0.0), (1.0, 1e-6, 0.0))
+    got = dict(pstar=sol.pstar, vstar=sol.vstar, rho_star_left=sol.waves[0][1],
+               rho_star_right=sol.waves[1][1])
+    for key, val, tol in _read_golden("marti_mueller_problem1.txt"):
+        assert abs(got[key] - float(val)) <= float(tol), (key, got[key], val)
+
+
+def test_paper_tube_states_match_fixture():
+    rows = {(r[0], r[1]): [float(v) for v in r[2:]] for r in _read_golden("paper_shock_tubes.txt")}
+    for case, (L, R) in {"sod": (W.SOD_LEFT, W.SOD_RIGHT),
+                         "balsara1": (W.BALSARA1_LEFT, W.BALSARA1_RIGHT)}.items():
+        for side, st in (("left", L), ("right", R)):
+            want = rows[(case, side)]
+            got = [st["rho"], st["p"], st.get("Bx", 0.0), st.get("By", 0.0), st.get("Bz", 0.0)]
+            assert got == want
+
+
+def _sod_l1(n, t_end=0.4):
+    P = W.sod(n, t_end=t_end)
+    grid, opts = _setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    prim, _, steps, t, nf = O.evolve(grid, opts, P.metric, P.prim, U, t_end, 0.5)
+    assert nf == 0 and abs(t - t_end) < 1e-14
+    sol = RiemannSolution(P.gamma, (1.0, 1.0, 0.0), (0.125, 0.1, 0.0))
+    xs = P.x0[0] + np.arange(n) * P.dx[0]
+    ex = np.array([sol.cell_average(x, x + P.dx[0], 0.0, t) for x in xs])
+    rho = prim[0].ravel()
+    W_ = np.sqrt(1.0 + prim[2].ravel() ** 2)
+    v = prim[2].ravel() / W_
+    return np.abs(rho - ex[:, 0]).mean(), np.abs(v - ex[:, 2]).mean(), np.abs(prim[1].ravel() - ex[:, 1]).mean()
+
+
+def test_sod_converges_to_exact_solution():
+    e100 = _sod_l1(100)
+    e400 = _sod_l1(400)
+    # shock-dominated: about first order; bound at N = 400 from the MC/HLLE dissipation
+    for a, b in zip(e100, e400):
+        assert b < a / 2.0
+    assert e400[0] < 3e-3 and e400[1] < 3e-3 and e400[2] < 3e-3
+
+
+# --------------------------------------------------------------------- conservation
+@pytest.mark.parametrize("dims", [(32, 1, 1), (12, 10, 8)])
+def test_conservation_periodic_minkowski(dims):
+    P = W.smooth_periodic(dims, seed=7, amp=0.2, magnetised=True)
+    grid, opts = _setup(P)
+    U0 = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    dt = 0.4 / O.max_speed(grid, opts, P.metric, P.prim)
+    prim, U = P.prim, U0
+    for _ in range(5):
+        prim, U, nf = O.step(grid, opts, P.metric, prim, U, dt)
+        assert nf == 0
+    tot0 = U0.reshape(9, -1).sum(axis=1)
+    tot = U.reshape(9, -1).sum(axis=1)
+    scale = np.abs(U0).reshape(9, -1).sum(axis=1) + 1e-300
+    assert np.all(np.abs(tot - tot0)[:8] <= 1e-13 * scale[:8]), (tot - tot0) / scale
+    assert np.abs(U - U0).max() > 1e-6  # something moved
+
+
+def _conformal_metric(X, Y, Z):
+    a = 0.8 + 0.1 * np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y)
+    psi4 = 1.2 + 0.1 * np.cos(2 * math.pi * Z) * np.sin(2 * math.pi * X)
+    m = np.zeros((10,) + X.shape)
+    m[0] = a
+    m[1] = 0.05 * np.sin(2 * math.pi * Y)
+    m[4] = m[7] = m[9] = psi4
+    m[5] = 0.02 * np.cos(2 * math.pi * Z)
+    return m
+
+
+def test_conservation_static_curved_periodic():
+    """With d_t g = 0 the energy source S_t vanishes: D, T_t, B are conserved exactly."""
+    P = W.smooth_periodic((10, 8, 6), seed=11, amp=0.2, magnetised=True)
+    P = W.with_periodic_metric(P, _conformal_metric)
+    grid, opts = _setup(P)
+    U0 = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    dt = 0.4 / O.max_speed(grid, opts, P.metric, P.prim)
+    prim, U = P.prim, U0
+    for _ in range(3):
+        prim, U, nf = O.step(grid, opts, P.metric, prim, U, dt)
+        assert nf == 0
+    d = (U - U0).reshape(9, -1).sum(axis=1)
+    scale = np.abs(U0).reshape(9, -1).sum(axis=1)
+    for f in (0, 1, 5, 6, 7):
+        assert abs(d[f]) <= 1e-13 * scale[f], (f, d[f] / scale[f])
+    # momentum is not conserved in a curved metric: its change equals dt-weighted sources
+    assert np.abs(d[2:5]).max() > 1e-10 * scale[2:5].max()
+
+
+# --------------------------------------------------------------------- recovery
+@pytest.mark.parametrize("cleaning", [False, True])
+def test_recovery_round_trip(cleaning):
+    n = 4000
+    met = W.random_metric_points(n, seed=21)
+    prim = W.random_prim_points(n, seed=22, met=met, wmax=10.0, sigma_max=100.0, cleaning=cleaning)
+    opts = O.make_opts(5.0 / 3.0, cleaning=cleaning, ch=0.5)
+    U = O.prim2cons(opts, met, prim)
+    rec, st, it = O.cons2prim(opts, met, U)
+    assert st.sum() == 0
+    # conserved round trip: well conditioned
+    U2 = O.prim2cons(opts, met, rec)
+    scale = np.abs(U).max(axis=1, keepdims=True)
+    assert np.abs(U2 - U).max() / 1.0 <= 1e-12 * scale.max() or np.all(np.abs(U2 - U) <= 1e-12 * scale)
+    # primitive round trip: rho, velocity, B to 1e-10; p scaled by its conditioning E/p
+    assert np.all(np.abs(rec[:, 0] - prim[:, 0]) <= 1e-10 * prim[:, 0])
+    st_ = O.state(opts, met, prim)
+    Wl = st_[:, 9]
+    E_over_p = (prim[:, 0] * Wl * Wl + 3 * prim[:, 1] * Wl * Wl + prim[:, 5:8].__pow__(2).sum(1)) / prim[:, 1]
+    assert np.all(np.abs(rec[:, 1] - prim[:, 1]) <= 1e-13 * prim[:, 1] * (1.0 + E_over_p) * 10)
+    vscale = np.abs(prim[:, 2:5]).max(axis=1) + 1.0
+    assert np.all(np.abs(rec[:, 2:5] - prim[:, 2:5]).max(axis=1) <= 1e-10 * vscale)
+    bscale = np.abs(prim[:, 5:8]).max(axis=1) + 1e-300
+    assert np.all(np.abs(rec[:, 5:8] - prim[:, 5:8]).max(axis=1) <= 1e-13 * bscale)
+    assert np.allclose(rec[:, 8], prim[:, 8], rtol=1e-13, atol=0)
+
+
+def test_recovery_independent_of_guess():
+    n = 500
+    met = W.random_metric_points(n, seed=31)
+    prim = W.random_prim_points(n, seed=32, met=met, wmax=5.0, sigma_max=10.0)
+    opts = O.make_opts(4.0 / 3.0)
+    U = O.prim2cons(opts, met, prim)
+    a, sa, _ = O.cons2prim(opts, met, U, guess=prim)
+    b, sb, _ = O.cons2prim(opts, met, U, guess=None)
+    assert sa.sum() == 0 and sb.sum() == 0
+    assert np.allclose(a, b, rtol=1e-11, atol=1e-14)
+
+
+def test_recovery_rejects_unphysical():
+    met = W.random_metric_points(3, seed=1)
+    opts = O.make_opts(2.0)
+    # E = (-T_t + beta^i T_i) / sqrt(-g), so T_t < 0 for a physical state
+    bad = np.array([[-1.0, -2.0, 0, 0, 0, 0, 0, 0, 0],      # D < 0
+                    [1.0, -1.5, 4.0, 0, 0, 0, 0, 0, 0],     # |S| > E
+                    [1.0, 1.0, 0, 0, 0, 0, 0, 0, 0]])       # E < 0
+    _, st, _ = O.cons2prim(opts, met, bad)
+    assert st.tolist() == [1, 1, 1]
+
+
+# --------------------------------------------------------------------- four-vectors, tensors
+def test_state_identities():
+    n = 300
+    met = W.random_metric_points(n, seed=41)
+    prim = W.random_prim_points(n, seed=42, met=met, wmax=8.0, sigma_max=50.0)
+    opts = O.make_opts(5.0 / 3.0)
+    s = O.state(opts, met, prim)
+    T, g4, g4i = O.tensors(opts, met, prim)
+    u, b = s[:, 0:4], s[:, 4:8]
+    ul = np.einsum("nab,nb->na", g4, u)
+    bl = np.einsum("nab,nb->na", g4, b)
+    assert np.allclose((u * ul).sum(1), -1.0, atol=1e-12 * (s[:, 9] ** 2).max())
+    assert np.all(np.abs((b * ul).sum(1)) <= 1e-12 * (np.abs(b).max(1) * np.abs(u).max(1) + 1e-300) * 10)
+    assert np.allclose((b * bl).sum(1), s[:, 8], rtol=1e-11, atol=1e-300)
+    w, p, b2 = s[:, 13], prim[:, 1], s[:, 8]
+    lhs = np.einsum("nab,na,nb->n", T, ul, ul)
+    assert np.allclose(lhs, w - p + 0.5 * b2, rtol=1e-9)
+    # g4 g4inv = identity
+    assert np.allclose(np.einsum("nab,nbc->nac", g4, g4i), np.eye(4)[None], atol=1e-12)
+
+
+def test_source_identity_against_christoffels():
+    rng = np.random.Generator(np.random.PCG64(51))
+    n = 200
+    met = W.random_metric_points(n, seed=52)
+    prim = W.random_prim_points(n, seed=53, met=met, wmax=4.0, sigma_max=10.0)
+    opts = O.make_opts(2.0)
+    T, g4, g4i = O.tensors(opts, met, prim)
+    dg = rng.normal(size=(n, 3, 4, 4))
+    dg = 0.5 * (dg + np.transpose(dg, (0, 1, 3, 2)))  # d_i g_ab symmetric in ab
+    src = O.source_pointwise(opts, met, dg.reshape(n, 48), prim)
+    # full Christoffel form: S_mu = sqrt(-g) T^k_l Gamma^l_{mu k}, static metric (d_t g = 0)
+    d4 = np.zeros((n, 4, 4, 4))
+    d4[:, 1:] = dg  # d4[:, c, a, b] = d_c g_ab
+    Gl = 0.5 * (np.einsum("ncab->nabc", d4) + np.einsum("nbac->nabc", d4) - np.einsum("nabc->nabc", d4))
+    # Gl[n, s, m, k] = Gamma_{s m k} = 1/2 (d_m g_sk + d_k g_sm - d_s g_mk)
+    Gl = 0.5 * (np.einsum("nmsk->nsmk", d4) + np.einsum("nksm->nsmk", d4) - np.einsum("nsmk->nsmk", d4))
+    Gam = np.einsum("nls,nsmk->nlmk", g4i, Gl)
+    Tmix = np.einsum("nka,nal->nkl", T, g4)  # T^k_l
+    sqrtmg = met[:, 0] * np.sqrt(np.linalg.det(np.stack([
+        np.stack([met[:, 4], met[:, 5], met[:, 6]], -1),
+        np.stack([met[:, 5], met[:, 7], met[:, 8]], -1),
+        np.stack([met[:, 6], met[:, 8], met[:, 9]], -1)], -2)))
+    want = sqrtmg[:, None] * np.einsum("nkl,nlmk->nm", Tmix, Gam)
+    scale = np.abs(want).max() + 1e-300
+    assert np.abs(src - want).max() <= 1e-12 * scale
+    assert np.all(src[:, 0] == 0.0)
+
+
+# --------------------------------------------------------------------- wave speeds
+def test_speeds_at_rest_are_fast_magnetosonic():
+    opts = O.make_opts(5.0 / 3.0)
+    met = np.tile(W.minkowski_metric((1, 1, 1)).reshape(10), (3, 1))
+    prim = np.array([[1.0, 0.5, 0, 0, 0, 0.0, 0.0, 0.0, 0],
+                     [1.0, 0.5, 0, 0, 0, 0.3, 0.7, -0.2, 0],
+                     [0.1, 2.0, 0, 0, 0, 1.0, 0.0, 0.0, 0]])
+    lam = O.speeds(opts, 0, met, prim)
+    g = 5.0 / 3.0
+    for r, (rho, p, *_rest) in enumerate(prim):
+        B = prim[r, 5:8]
+        w = rho + g / (g - 1) * p
+        cs2 = g * p / w
+        b2 = float(B @ B)
+        va2 = b2 / (w + b2)
+        c = math.sqrt(cs2 + va2 - cs2 * va2)
+        assert lam[r, 1] == pytest.approx(c, rel=1e-14) and lam[r, 0] == pytest.approx(-c, rel=1e-14)
+
+
+def test_speeds_boosted_sound_velocity_addition():
+    g = 4.0 / 3.0
+    opts = O.make_opts(g)
+    rho, p = 1.0, 0.7
+    cs = math.sqrt(g * p / (rho + g / (g - 1) * p))
+    met = np.tile(W.minkowski_metric((1, 1, 1)).reshape(10), (5, 1))
+    vs = np.array([-0.9, -0.3, 0.0, 0.5, 0.95])
+    prim = np.zeros((5, 9))
+    prim[:, 0], prim[:, 1] = rho, p
+    prim[:, 2] = vs / np.sqrt(1 - vs * vs)
+    lam = O.speeds(opts, 0, met, prim)
+    assert np.allclose(lam[:, 1], (vs + cs) / (1 + vs * cs), rtol=1e-13)
+    assert np.allclose(lam[:, 0], (vs - cs) / (1 - vs * cs), rtol=1e-13, atol=1e-15)
+    # transverse direction: lambda = +-cs sqrt(1 - v^2) / sqrt(1 - v^2 cs^2) for v along x
+    lam_y = O.speeds(opts, 1, met, prim)
+    want = cs * np.sqrt(1 - vs * vs) / np.sqrt(1 - vs * vs * cs * cs)
+    assert np.allclose(lam_y[:, 1], want, rtol=1e-12)
+
+
+# --------------------------------------------------------------------- induction sign
+def _advected_field(n, t_end=0.2):
+    """v^x = 0.5, B^y = 0.5 sin(2 pi x), total pressure uniform: exact translation at 0.5."""
+    dx = 1.0 / n
+    xs = (np.arange(n) + 0.5) * dx
+    v = 0.5
+    Wl = 1.0 / math.sqrt(1 - v * v)
+    By = 0.5 * np.sin(2 * math.pi * xs)
+    prim = np.zeros((9, 1, 1, n))
+    prim[0] = 1.0 + 0.2 * np.sin(2 * math.pi * xs)
+    prim[1] = 1.0 - By ** 2 / (2 * Wl * Wl)
+    prim[2] = Wl * v
+    prim[6] = By
+    P = W.Problem("adv", (n, 1, 1), (dx, 1.0, 1.0), (0.0, 0.0, 0.0), (1, 1, 1), 5.0 / 3.0,
+                  prim, W.minkowski_metric((n, 1, 1)))
+    grid, opts = _setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    out, _, _, t, nf = O.evolve(grid, opts, P.metric, P.prim, U, t_end, 0.4)
+    assert nf == 0
+    exact_By = 0.5 * np.sin(2 * math.pi * (xs - v * t))
+    wrong_By = 0.5 * np.sin(2 * math.pi * (xs + v * t))
+    got = out[6].ravel()
+    return np.abs(got - exact_By).mean(), np.abs(got - wrong_By).mean(), out
+
+
+def test_induction_sign_advects_with_flow():
+    err, err_wrong, out = _advected_field(128)
+    assert err < 2e-3 and err_wrong > 0.1
+    # total pressure stays uniform: no spurious acceleration
+    assert np.abs(out[3:5]).max() < 1e-12
+
+
+# --------------------------------------------------------------------- invariants
+def test_balsara_bx_exactly_constant_and_uniform_state_stationary():
+    P = W.balsara1(200)
+    grid, opts = _setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    out, Uo, steps, t, nf = O.evolve(grid, opts, P.metric, P.prim, U, 0.1, 0.5)
+    assert nf == 0
+    assert np.all(out[5] == 0.5)
+    assert np.all(Uo[5] == 0.5)
+    # uniform moving magnetised state in Minkowski: L(U) = 0 exactly
+    n = (6, 5, 4)
+    prim = np.zeros((9,) + n[::-1])
+    prim[:] = np.array([0.7, 0.3, 0.2, -0.1, 0.4, 0.3, 0.5, -0.6, 0.0])[:, None, None, None]
+    g = O.make_grid(n, (0.1, 0.1, 0.1), (0, 0, 0))
+    L = O.rhs(g, O.make_opts(5 / 3), W.minkowski_metric(n), prim)
+    assert np.all(L == 0.0)
+
+
+def test_tube_direction_symmetry():
+    outs = []
+    for axis in range(3):
+        P = W.balsara1(100, axis=axis)
+        grid, opts = _setup(P)
+        U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+        out, _, steps, t, nf = O.evolve(grid, opts, P.metric, P.prim, U, 0.1, 0.5)
+        perm = [(0, 1, 2), (1, 2, 0), (2, 0, 1)][axis]
+        vec = np.stack([out[2 + perm[k]].ravel() for k in range(3)] +
+                       [out[5 + perm[k]].ravel() for k in range(3)])
+        outs.append(np.concatenate([out[0].ravel()[None], out[1].ravel()[None], vec]))
+    for o in outs[1:]:
+        assert np.allclose(o, outs[0], rtol=1e-12, atol=1e-13)
+
+
+def test_mirror_symmetry():
+    P = W.balsara1(100)
+    grid, opts = _setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    out, *_ = O.evolve(grid, opts, P.metric, P.prim, U, 0.1, 0.5)
+    # mirror x -> -x with swapped states: rho, p even; u~x odd; B^x odd, B^y, B^z even
+    Pm = W.shock_tube(100, dict(W.BALSARA1_RIGHT, Bx=-0.5), dict(W.BALSARA1_LEFT, Bx=-0.5), 2.0, 0.4)
+    Um = O.grid_prim2cons(grid, opts, Pm.metric, Pm.prim)
+    outm, *_ = O.evolve(grid, opts, Pm.metric, Pm.prim, Um, 0.1, 0.5)
+    sgn = np.array([1, 1, -1, 1, 1, -1, 1, 1, 1])
+    mir = sgn[:, None] * outm.reshape(9, -1)[:, ::-1]
+    assert np.allclose(out.reshape(9, -1), mir, rtol=1e-12, atol=1e-13)
+
+
+# --------------------------------------------------------------------- convergence
+def _entropy_wave(n, t_end, dt=None):
+    dx = 1.0 / n
+    xs = (np.arange(n) + 0.5) * dx
+    v = 0.5
+    Wl = 1.0 / math.sqrt(1 - v * v)
+    prim = np.zeros((9, 1, 1, n))
+    # cell averages of 1 + 0.2 sin(2 pi x)
+    prim[0] = 1.0 + 0.2 * (np.cos(2 * math.pi * (xs - dx / 2)) - np.cos(2 * math.pi * (xs + dx / 2))) / (2 * math.pi * dx)
+    prim[1] = 1.0
+    prim[2] = Wl * v
+    P = W.Problem("ent", (n, 1, 1), (dx, 1.0, 1.0), (0.0, 0.0, 0.0), (1, 1, 1), 5.0 / 3.0,
+                  prim, W.minkowski_metric((n, 1, 1)))
+    grid, opts = _setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    out, _, _, t, nf = O.evolve(grid, opts, P.metric, P.prim, U, t_end, 0.4, fixed_dt=dt or 0.0)
+    exact = 1.0 + 0.2 * (np.cos(2 * math.pi * (xs - dx / 2 - v * t)) - np.cos(2 * math.pi * (xs + dx / 2 - v * t))) / (2 * math.pi * dx)
+    return out[0].ravel(), exact
+
+
+def test_smooth_wave_second_order_in_space():
+    errs = []
+    for n in (32, 64, 128):
+        rho, ex = _entropy_wave(n, 0.4)
+        errs.append(np.abs(rho - ex).mean())
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert orders[-1] > 1.6, (errs, orders)
+
+
+def _ramp(n, t_end, nsteps):
+    """Monotone smooth data with outflow boundaries: the MC limiter keeps one branch per cell,
+    so the semi-discrete system is smooth and the time error shows the RK order."""
+    dx = 1.0 / n
+    xs = (np.arange(n) + 0.5) * dx
+    prim = np.zeros((9, 1, 1, n))
+    prim[0] = 1.0 + 0.3 * xs
+    prim[1] = 1.0 + 0.2 * xs * xs
+    prim[2] = 0.4 + 0.1 * xs
+    prim[6] = 0.3 + 0.2 * xs
+    P = W.Problem("ramp", (n, 1, 1), (dx, 1.0, 1.0), (0.0, 0.0, 0.0), (0, 0, 0), 5.0 / 3.0,
+                  prim, W.minkowski_metric((n, 1, 1)))
+    grid, opts = _setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    out, *_ = O.evolve(grid, opts, P.metric, P.prim, U, t_end, 0.4, fixed_dt=t_end / nsteps)
+    return out[:, 0, 0, n // 4: 3 * n // 4]
+
+
+def test_rk3_third_order_in_time():
+    sols = [_ramp(32, 0.05, k) for k in (10, 20, 40)]
+    e1 = np.abs(sols[0] - sols[1]).max()
+    e2 = np.abs(sols[1] - sols[2]).max()
+    assert math.log2(e1 / e2) > 2.7, (e1, e2)
+
+
+# --------------------------------------------------------------------- divergence cleaning
+def _glm_wave(n, ch, kappa, t_end, B0=1e-4):
+    """Uniform gas at rest with a divergence error B^x = B0 sin(2 pi x): the cleaning pair obeys
+    d_t B + d_x psi = 0, d_t psi + c_h^2 d_x B = -kappa psi (to O(B0^2))."""
+    dx = 1.0 / n
+    xs = (np.arange(n) + 0.5) * dx
+    prim = np.zeros((9, 1, 1, n))
+    prim[0] = 1.0
+    prim[1] = 1.0
+    prim[5] = B0 * (np.cos(2 * math.pi * (xs - dx / 2)) - np.cos(2 * math.pi * (xs + dx / 2))) / (2 * math.pi * dx)
+    P = W.Problem("glm", (n, 1, 1), (dx, 1.0, 1.0), (0.0, 0.0, 0.0), (1, 1, 1), 5.0 / 3.0,
+                  prim, W.minkowski_metric((n, 1, 1)), cleaning=True, ch=ch, kappa=kappa)
+    grid, opts = _setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    out, _, _, t, nf = O.evolve(grid, opts, P.metric, P.prim, U, t_end, 0.4)
+    assert nf == 0
+    return xs, prim, out
+
+
+def test_cleaning_wave_speed_and_sign():
+    ch = 0.5
+    # half an oscillation period of the k = 2 pi mode: B^x -> -B^x
+    xs, p0, out = _glm_wave(64, ch, 0.0, 1.0 / (2 * ch))
+    b0, b1 = p0[5].ravel(), out[5].ravel()
+    assert np.abs(b1 + b0).max() < 0.03 * np.abs(b0).max()
+    # a quarter period later than that the field passes through zero and psi peaks at c_h B0
+    xs, p0, out = _glm_wave(64, ch, 0.0, 1.0 / (4 * ch))
+    assert np.abs(out[5]).max() < 0.03 * np.abs(p0[5]).max()
+    assert abs(np.abs(out[8]).max() / (ch * np.abs(p0[5]).max()) - 1.0) < 0.03
+
+
+def test_cleaning_damping_rate():
+    ch, kappa, t = 0.5, 2.0, 0.5
+    xs, p0, out = _glm_wave(64, ch, kappa, t)
+    e0 = (p0[5] ** 2).sum()
+    e1 = (out[5] ** 2).sum() + (out[8] ** 2).sum() / ch ** 2
+    xs, p0u, outu = _glm_wave(64, ch, 0.0, t)
+    e1u = (outu[5] ** 2).sum() + (outu[8] ** 2).sum() / ch ** 2
+    # undamped: energy of the pair conserved up to the scheme's dissipation; damped: e^{-kappa t}
+    assert abs(e1u / e0 - 1.0) < 0.02
+    ratio = (e1 / e0) / (e1u / e0)
+    # damped oscillator of the k = 2 pi mode: B'' + kappa B' + (c_h k)^2 B = 0, B(0)=1, B'(0)=0;
+    # psi = B' / k, pair energy B^2 + psi^2 / c_h^2
+    k = 2 * math.pi
+    w = math.sqrt((ch * k) ** 2 - kappa ** 2 / 4)
+    Bt = math.exp(-kappa * t / 2) * (math.cos(w * t) + kappa / (2 * w) * math.sin(w * t))
+    dBt = -math.exp(-kappa * t / 2) * ((ch * k) ** 2 / w) * math.sin(w * t)
+    want = Bt ** 2 + (dBt / (k * ch)) ** 2
+    assert abs(ratio / want - 1.0) < 0.03, (ratio, want)
+
+
+def test_cleaning_keeps_1d_bx_constant():
+    P = W.balsara1(100)
+    P.cleaning, P.ch, P.kappa = True, 1.0, 1.0
+    grid, opts = _setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    out, Uo, *_ = O.evolve(grid, opts, P.metric, P.prim, U, 0.1, 0.5)
+    assert np.all(out[5] == 0.5) and np.all(out[8] == 0.0)
