@@ -1,0 +1,359 @@
+"""Benchmark of the GB300 GRMHD finite-volume hot path: zone-updates per second.
+
+Workload (N = 1): the 3-D GRMHD blob in a fixed capped-Schwarzschild spacetime, 192^3 cells
+on [-20, 20]^3, FP64, divergence cleaning on, seed 1102 (the paper's rotating-neutron-star
+runs of §4.1 need the external rns code; this seeded blob has their shape).  One "step" is
+one full RK3 step (three fused substep launches plus the device time-step clock) over the
+whole grid.  The state (about 2.6 GB) is larger than L2, so no flush is needed between steps.
+
+Lines printed (one JSON line on rank 0):
+  default          the CUDA path: device-timed value, roofline of the substep kernel, the
+                   oracle's CPU baseline on a bounded sample, an end-to-end number through
+                   the C-ABI with host buffers, SM clocks sampled during the timed region;
+  --impl reference the FP64 oracle on the host cores on a bounded sample of the same
+                   workload (the reference arm: a deliberately slow, plain program).
+Under torchrun (N > 1) every rank advances its own independent replica (the path is not
+sharded across GPUs): value = all ranks' zone updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s"
+UNIT = "ZU/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA throughput measured on this machine's GB300 with an in-register DFMA loop
+# (profiles/fp64_alu_peak.md): 2 DFMA per clock per SM x 152 SMs.
+FP64_PEAK_TFLOPS = 1.194
+# FP64 operations per cell per substep executed by the fused substep kernel (3-D, cleaning
+# on), from ncu instruction counters on the 64^3 blob (profiles/k_substep_blob3d.md):
+# DFMA counted as 2 flops, DADD/DMUL as 1.
+FP64_FLOPS_PER_CELL_SUBSTEP = None
+# Algorithmic HBM bytes per zone update (three substeps, FP64, nine fields): read P, U_k, U0,
+# metric and write U_{k+1}, P_{k+1} once per substep; stage 1 reads U0 once.
+HBM_BYTES_PER_ZU = (46 + 55 + 55) * 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=192, help="cells per axis of the blob")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def aggregate(units_local: float, seconds_local: float, dist, device=None):
+    """Whole-job throughput: sum of units over ranks / max of time over ranks."""
+    if dist is None:
+        return units_local, seconds_local
+    import torch
+
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    t = torch.tensor([seconds_local], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm = float(parts[1].split()[0])
+                smax = float(parts[2].split()[0])
+            except ValueError:
+                continue
+            rows.append((sm, smax, parts[5], parts[6], parts[7], parts[8]))
+        if not rows:
+            return None
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, v in zip(names, r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local):
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+    from paper_1102_5202_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    P = W.blob3d(args.n)
+    s = hzn.Solver.for_problem(P)
+    stream = s.stream
+    cells = P.ncell
+
+    for _ in range(args.warmup):
+        s.step_cfl(0.5, 1e30)
+    torch.cuda.synchronize()
+    st0 = s.stats()
+    if st0.c2p_failures:
+        print(f"[rank {rank}] warning: {st0.c2p_failures} recovery failures in warm-up", file=sys.stderr)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_stop = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            s.step_cfl(0.5, 1e30)
+            ev[k][1].record(stream)
+        t_stop.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_stop) * 1e-3
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st = s.stats()
+    units, seconds = aggregate(float(cells) * args.steps, elapsed, dist, device=torch.device("cuda", local))
+    value = units / seconds
+
+    # roofline of the dominant kernel (the fused substep): three launches per step
+    substep_s = statistics.mean(step_ms) * 1e-3 / 3.0
+    if FP64_FLOPS_PER_CELL_SUBSTEP:
+        ach = FP64_FLOPS_PER_CELL_SUBSTEP * cells / substep_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_substep<32,4,3-D,cleaning>", "peak_source": "measured FP64 DFMA loop"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "kernel": "k_substep<32,4,3-D,cleaning>"}
+    hbm_peak = json.load(open(MEASURED_PEAKS))["hbm_gbs"] if os.path.exists(MEASURED_PEAKS) else 6800.0
+    hbm_ach = HBM_BYTES_PER_ZU / 3.0 * cells / substep_s / 1e9
+    hbm = {"bytes_per_zu": HBM_BYTES_PER_ZU, "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+           "frac": hbm_ach / hbm_peak, "roofline_zu_per_s": hbm_peak * 1e9 / HBM_BYTES_PER_ZU,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs" if os.path.exists(MEASURED_PEAKS) else "fallback"}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(s, P, args, dist, local)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = run_cpu_baseline(P, seconds_target=15.0)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": seconds / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"blob3d_{args.n}^3_fp64_cleaning", "cells": cells,
+                       "domain": "[-20,20]^3", "metric": "capped isotropic Schwarzschild M=1.4",
+                       "cfl": 0.5, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state larger than L2 (no flush)"},
+            "roofline": roof,
+            "hbm_roofline": hbm,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+            "c2p_failures": int(st.c2p_failures),
+            "sim_time": st.t,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def run_e2e(s, P, args, dist, local):
+    """Same metric through the C-ABI with the state in pinned host memory: every step copies
+    the primitive state host->device, converts it, advances one RK3 step and copies the new
+    primitive state back."""
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+
+    host_in = torch.from_numpy(np.ascontiguousarray(P.prim)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_in = torch.empty(host_in.shape, dtype=torch.float64, device=s.device)
+    dev_out = torch.empty_like(dev_in)
+    stream = s.stream
+    nsteps = max(3, min(args.steps, 10))
+
+    def one():
+        dev_in.copy_(host_in, non_blocking=True)
+        hzn.hz_set_primitives(s.ctx, dev_in.data_ptr())
+        hzn.hz_step_cfl(s.ctx, 0.5, 1e30)
+        hzn.hz_get_primitives(s.ctx, dev_out.data_ptr())
+        host_out.copy_(dev_out, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        one()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(nsteps):
+            one()
+        b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) * 1e-3
+    units, seconds = aggregate(float(P.ncell) * nsteps, sec, dist, device=torch.device("cuda", local))
+    nbytes = host_in.numel() * 8
+    # restore the benchmark state
+    s.set_primitives(P.prim)
+    return {"value": units / seconds, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "steps": nsteps}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample(P, m: int):
+    """Central m^3 sub-box of the workload with its metric (the sample the oracle times)."""
+    lo = (P.n[0] - m) // 2
+    return P.subbox((lo,) * 3, (lo + m,) * 3, name=f"{P.name}_sample{m}")
+
+
+def run_cpu_baseline(P, seconds_target=15.0, m=48):
+    import oracle as O
+
+    Q = oracle_sample(P, m)
+    grid = O.make_grid(Q.n, Q.dx, Q.bc)
+    opts = O.make_opts(Q.gamma, cleaning=Q.cleaning, ch=Q.ch, kappa=Q.kappa, rho_floor=Q.rho_floor,
+                       p_floor=Q.p_floor, atm_K=Q.atm_K, rho_atm=Q.rho_atm)
+    U = O.grid_prim2cons(grid, opts, Q.metric, Q.prim)
+    dt = 0.5 / O.max_speed(grid, opts, Q.metric, Q.prim)
+    prim, cons = Q.prim, U
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        prim, cons, _ = O.step(grid, opts, Q.metric, prim, cons, dt)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds_target or steps >= 1000:
+            break
+    sec = time.perf_counter() - t0
+    return {"value": Q.ncell * steps / sec, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{steps} RK3 step(s) of the central {m}^3 sub-box of the {P.n[0]}^3 blob, "
+                      f"{sec:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_1102_5202_gb300 import workloads as W
+
+    import oracle as O
+
+    P = W.blob3d(args.n)
+    m = 32
+    Q = oracle_sample(P, m)
+    grid = O.make_grid(Q.n, Q.dx, Q.bc)
+    opts = O.make_opts(Q.gamma, cleaning=Q.cleaning, ch=Q.ch, kappa=Q.kappa, rho_floor=Q.rho_floor,
+                       p_floor=Q.p_floor, atm_K=Q.atm_K, rho_atm=Q.rho_atm)
+    U = O.grid_prim2cons(grid, opts, Q.metric, Q.prim)
+    dt = 0.5 / O.max_speed(grid, opts, Q.metric, Q.prim)
+    prim, cons = Q.prim, U
+    for _ in range(args.warmup):
+        prim, cons, _ = O.step(grid, opts, Q.metric, prim, cons, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        prim, cons, _ = O.step(grid, opts, Q.metric, prim, cons, dt)
+    sec = time.perf_counter() - t0
+    value = Q.ncell * args.steps / sec
+    sample = f"each step: one RK3 step of the central {m}^3 sub-box of the {args.n}^3 blob"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"blob3d_{args.n}^3_fp64_cleaning", "cells": P.ncell,
+                       "sample_cells": Q.ncell, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return line
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+/* hzn.h -- C-ABI of the GB300 GRMHD finite-volume library (libhzn.so, sm_103a).
+ *
+ * The library advances the conservation form of ideal general-relativistic MHD in a fixed
+ * spacetime (§2.1 Eq. 2, compact form §2.2 Eq. 3) on a uniform Cartesian mesh with the
+ * scheme of §2.2/§3.2: MC-limited reconstruction of the primitive variables, HLLE fluxes,
+ * flux divergence plus metric source, third-order Runge-Kutta, Newton-Raphson recovery of
+ * the primitive variables and hyperbolic divergence cleaning.  One full RK3 step is three
+ * fused stencil launches (one per substep) on the caller's CUDA stream.
+ *
+ * Conventions shared by every call
+ *   - Return value: HZ_OK (0) on success, a negative HZ_ERR_* on error, HZ_WARN_C2P (> 0)
+ *     when the call completed but cells were reset to atmosphere (count in hz_stats).
+ *     No call aborts, throws or prints.  hz_strerror() names every code.
+ *   - Pointers named d_* are CUDA device pointers owned by the caller; the library never
+ *     frees them and never keeps them beyond the call (inputs are copied into the workspace).
+ *     Host pointers are named h_* or are plain out-parameters.
+ *   - Grid functions are field-major, x fastest, no padding: field f of cell (i, j, k) is at
+ *     [f * N + (k * ny + j) * nx + i], N = nx * ny * nz.  The metric carries one ghost layer
+ *     on every active axis (an axis with n > 1): Nm = (nx + 2gx)(ny + 2gy)(nz + 2gz), g = 1
+ *     on an active axis and 0 otherwise, and cell (i, j, k) sits at (i + gx, j + gy, k + gz).
+ *   - Primitive fields (9): rho, p, u~^x, u~^y, u~^z, B^x, B^y, B^z, psi.  u~^i = W v^i =
+ *     u^i + W beta^i / alpha is the primitive velocity of §5.2 (footnote); B^i = *F^{it} (§2.1);
+ *     psi is the divergence-cleaning scalar (ignored and kept 0 when cleaning is off).
+ *   - Conserved fields (9): sqrt(-g) rho u^t, sqrt(-g) T^t_t, sqrt(-g) T^t_x,y,z,
+ *     sqrt(-g) B^x,y,z (§2.1, the eight conservative quantities), Psi = sqrt(gamma) psi.
+ *   - Metric fields (10): alpha, beta^x, beta^y, beta^z, gamma_xx, _xy, _xz, _yy, _yz, _zz.
+ *   - All device work is enqueued on the stream given to hz_create and is asynchronous unless
+ *     the call says it synchronises.  A context must not be used from two host threads at once.
+ */
+#ifndef HZN_H
+#define HZN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HZN_VERSION 1
+
+enum {
+  HZ_OK = 0,
+  HZ_WARN_C2P = 1,       /* completed; some cells were reset to atmosphere              */
+  HZ_ERR_ARG = -1,       /* invalid argument (null pointer, bad size, bad option)        */
+  HZ_ERR_CUDA = -2,      /* a CUDA runtime call failed (the context may be unusable)     */
+  HZ_ERR_STATE = -3,     /* call out of order (e.g. step before metric and primitives)   */
+  HZ_ERR_WORKSPACE = -4, /* workspace pointer misaligned or smaller than required        */
+  HZ_ERR_UNSUPPORTED = -5/* option combination not built                                 */
+};
+
+enum { HZ_BC_OUTFLOW = 0, HZ_BC_PERIODIC = 1 };
+enum { HZ_FP64 = 0, HZ_MIXED = 1 };
+
+typedef struct hz_ctx hz_ctx; /* opaque; host-side bookkeeping, owned by the library */
+
+/* Uniform Cartesian mesh.  An axis with n = 1 is inactive (no flux, no metric derivative).
+ * Active axes need n >= 2; outflow boundaries copy the nearest interior cell (zero gradient),
+ * periodic ones wrap. */
+typedef struct {
+  int n[3];
+  int bc[3];
+  double dx[3];
+} hz_grid;
+
+/* Physics and numerics options (§3.2 lists the scheme choices; the values are run inputs). */
+typedef struct {
+  double gamma;     /* ideal-gas index, p = (gamma - 1) rho eps; 1 < gamma <= 3          */
+  int precision;    /* HZ_FP64 (every step in FP64) | HZ_MIXED (reserved)                   */
+  int cleaning;     /* 1: hyperbolic divergence cleaning with the field psi (§3.2)         */
+  double ch;        /* cleaning speed as a fraction of light speed (0 < ch <= 1)          */
+  double kappa;     /* cleaning damping rate (>= 0)                                       */
+  double rho_floor; /* atmosphere density; a recovered rho below it resets the cell        */
+  double rho_atm;   /* a cell whose D / sqrt(gamma) (= rho W) is below rho_atm is set to the
+                       atmosphere without a recovery (0 disables)                           */
+  double p_floor;   /* pressure floor                                                    */
+  double atm_K;     /* atmosphere pressure = atm_K rho_floor^gamma when > 0, else p_floor */
+  int c2p_maxit;    /* Newton iteration cap of the recovery (1 .. 200)                    */
+  double c2p_tol;   /* Newton stop: |dZ| <= c2p_tol Z (1e-15 .. 1e-6)                     */
+} hz_options;
+
+typedef struct {
+  long long c2p_failures; /* cells reset to atmosphere since the last hz_set_primitives     */
+  int c2p_max_iters;      /* largest Newton iteration count seen since then                 */
+  double max_speed;       /* max over cells and active axes of max|lambda|/dx, newest state */
+  double t;               /* simulated time since the last hz_set_primitives               */
+  double dt;              /* step size of the last step                                     */
+  long long steps;        /* full RK3 steps since the last hz_set_primitives               */
+} hz_stats;
+
+/* Device bytes the caller must provide to hz_create for this grid and options.
+ * Errors: HZ_ERR_ARG for null pointers or invalid grid/options. */
+int hz_workspace_bytes(const hz_grid* grid, const hz_options* opts, size_t* bytes);
+
+/* Create a context on the current CUDA device.  d_workspace: caller-owned device memory of at
+ * least hz_workspace_bytes, 256-byte aligned, valid until hz_destroy; the library allocates
+ * no device memory of its own.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: HZ_ERR_ARG, HZ_ERR_WORKSPACE, HZ_ERR_UNSUPPORTED, HZ_ERR_CUDA. */
+int hz_create(hz_ctx** ctx, const hz_grid* grid, const hz_options* opts, void* d_workspace,
+              size_t bytes, void* stream);
+
+/* Release the host-side context (the workspace stays with the caller).  Null is accepted. */
+int hz_destroy(hz_ctx* ctx);
+
+/* Copy the metric at cell centres, ghost layer included (10 x Nm doubles, layout above) into
+ * the workspace.  The metric is the fixed spacetime of §2.1 (Cowling approximation). */
+int hz_set_metric(hz_ctx* ctx, const double* d_metric);
+
+/* Copy the primitive state (9 x N doubles) into the workspace and compute the conserved
+ * state w(u) per cell (§2.2: algebraic).  Resets time, step count and statistics, and
+ * computes the maximum characteristic speed of the new state.  Requires hz_set_metric. */
+int hz_set_primitives(hz_ctx* ctx, const double* d_prim);
+
+/* Copy out the current primitive / conserved state (9 x N doubles each). */
+int hz_get_primitives(hz_ctx* ctx, double* d_prim);
+int hz_get_conserved(hz_ctx* ctx, double* d_cons);
+
+/* One full RK3 step (three substeps, §3.2) of size dt > 0, asynchronous on the stream. */
+int hz_step(hz_ctx* ctx, double dt);
+
+/* One full RK3 step with dt = cfl / max_speed taken on the device from the newest state and
+ * clipped so that t does not pass t_end (dt = 0 once t = t_end).  Asynchronous: no host
+ * synchronisation, so a sequence of calls can be captured in a CUDA graph. */
+int hz_step_cfl(hz_ctx* ctx, double cfl, double t_end);
+
+/* Maximum over cells and active axes of max(|lambda+|, |lambda-|)/dx of the current state
+ * (with the cleaning speed when cleaning is on).  Synchronises the stream. */
+int hz_max_speed(hz_ctx* ctx, double* h_out);
+
+/* Statistics of the run so far.  Synchronises the stream.  Returns HZ_WARN_C2P when
+ * c2p_failures > 0. */
+int hz_get_stats(hz_ctx* ctx, hz_stats* h_out);
+
+/* Static description of a return code. */
+const char* hz_strerror(int code);
+
+/* HZN_VERSION of the loaded library. */
+int hz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZN_H */

@@ -43,6 +43,7 @@ class Opts(ctypes.Structure):
         ("p_floor", ctypes.c_double),
         ("atm_K", ctypes.c_double),
         ("c2p_maxit", ctypes.c_int),
+        ("rho_atm", ctypes.c_double),
     ]
 
 
@@ -102,9 +103,9 @@ def _f64(a) -> np.ndarray:
 
 def make_opts(gamma: float, cleaning: bool = False, ch: float = 0.0, kappa: float = 0.0,
               rho_floor: float = 1e-12, p_floor: float = 1e-14, atm_K: float = 0.0,
-              c2p_maxit: int = 200) -> Opts:
+              c2p_maxit: int = 200, rho_atm: float = 0.0) -> Opts:
     return Opts(float(gamma), int(bool(cleaning)), float(ch), float(kappa), float(rho_floor),
-                float(p_floor), float(atm_K), int(c2p_maxit))
+                float(p_floor), float(atm_K), int(c2p_maxit), float(rho_atm))
 
 
 def make_grid(n, dx, bc) -> Grid:

@@ -69,6 +69,7 @@ typedef struct {
   double p_floor;    // pressure floor
   double atm_K;      // atmosphere pressure = atm_K rho_floor^gamma if > 0, else p_floor
   int c2p_maxit;     // iteration cap of the recovery
+  double rho_atm;    // cells with D / sqrt(gamma) below rho_atm are set to the atmosphere (0: off)
 } hzo_opts;
 
 }  // extern "C"
@@ -400,9 +401,14 @@ static int con2prim(const Geom& G, const double U[NCONS], const double Pguess[NP
 // Recovery plus atmosphere / floor treatment; may rewrite U.  Returns 1 if the cell was reset.
 static int recover_cell(const Geom& G, double U[NCONS], const double Pguess[NPRIM],
                         const hzo_opts& o, double P[NPRIM], int* iters) {
-  int fail = con2prim(G, U, Pguess, o, P, iters);
+  // atmosphere: a cell whose rest-mass density D / sqrt(gamma) = rho W is below rho_atm is
+  // not recovered but set to the atmosphere state (the decision uses the conserved state only)
+  const bool atm = o.rho_atm > 0.0 && U[CD] / G.sqrtgam < o.rho_atm;
+  int fail = 0;
+  *iters = 0;
+  if (!atm) fail = con2prim(G, U, Pguess, o, P, iters);
   int reset = 0;
-  if (fail || P[RHO] < o.rho_floor) {
+  if (atm || fail || P[RHO] < o.rho_floor) {
     double Bkeep[3] = {U[CBX] / G.sqrtmg, U[CBY] / G.sqrtmg, U[CBZ] / G.sqrtmg};
     P[RHO] = o.rho_floor;
     P[PRS] = o.atm_K > 0.0 ? o.atm_K * std::pow(o.rho_floor, o.gamma) : o.p_floor;

@@ -1,0 +1,298 @@
+"""Thin Python binding of libhzn (the C-ABI declared in include/hzn.h).
+
+The functions ``hz_*`` below have the names, arguments and return codes of the C calls; they
+only marshal arguments.  Device memory and streams come from PyTorch (``torch.empty`` on the
+CUDA device, ``torch.cuda.current_stream()``); every step of the numerical method runs in the
+library's CUDA kernels.  ``Solver`` bundles the calls for one grid.
+
+The library is loaded on first use.  If it is missing or fails to load, ``lib()`` raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+HZ_OK, HZ_WARN_C2P = 0, 1
+HZ_ERR_ARG, HZ_ERR_CUDA, HZ_ERR_STATE, HZ_ERR_WORKSPACE, HZ_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+HZ_BC_OUTFLOW, HZ_BC_PERIODIC = 0, 1
+HZ_FP64, HZ_MIXED = 0, 1
+
+EXPORTED = (
+    "hz_workspace_bytes", "hz_create", "hz_destroy", "hz_set_metric", "hz_set_primitives",
+    "hz_get_primitives", "hz_get_conserved", "hz_step", "hz_step_cfl", "hz_max_speed",
+    "hz_get_stats", "hz_strerror", "hz_version",
+)
+
+
+class hz_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("bc", ctypes.c_int * 3), ("dx", ctypes.c_double * 3)]
+
+
+class hz_options(ctypes.Structure):
+    _fields_ = [
+        ("gamma", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("cleaning", ctypes.c_int),
+        ("ch", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("rho_floor", ctypes.c_double),
+        ("rho_atm", ctypes.c_double),
+        ("p_floor", ctypes.c_double),
+        ("atm_K", ctypes.c_double),
+        ("c2p_maxit", ctypes.c_int),
+        ("c2p_tol", ctypes.c_double),
+    ]
+
+
+class hz_stats(ctypes.Structure):
+    _fields_ = [
+        ("c2p_failures", ctypes.c_longlong),
+        ("c2p_max_iters", ctypes.c_int),
+        ("max_speed", ctypes.c_double),
+        ("t", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("steps", ctypes.c_longlong),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HznError(RuntimeError):
+    def __init__(self, code: int, call: str):
+        super().__init__(f"{call} failed: {code} ({hz_strerror(code)})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libhzn.so (raises if it was not built; ``build.build_library()`` builds it)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libhzn.so is not built ({path}); run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            P = ctypes.POINTER
+            vp, dp = ctypes.c_void_p, P(ctypes.c_double)
+            L.hz_workspace_bytes.argtypes = [P(hz_grid), P(hz_options), P(ctypes.c_size_t)]
+            L.hz_create.argtypes = [P(vp), P(hz_grid), P(hz_options), vp, ctypes.c_size_t, vp]
+            L.hz_destroy.argtypes = [vp]
+            L.hz_set_metric.argtypes = [vp, vp]
+            L.hz_set_primitives.argtypes = [vp, vp]
+            L.hz_get_primitives.argtypes = [vp, vp]
+            L.hz_get_conserved.argtypes = [vp, vp]
+            L.hz_step.argtypes = [vp, ctypes.c_double]
+            L.hz_step_cfl.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+            L.hz_max_speed.argtypes = [vp, dp]
+            L.hz_get_stats.argtypes = [vp, P(hz_stats)]
+            L.hz_strerror.argtypes = [ctypes.c_int]
+            L.hz_strerror.restype = ctypes.c_char_p
+            L.hz_version.restype = ctypes.c_int
+            for name in EXPORTED:
+                if name not in ("hz_strerror", "hz_version"):
+                    getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ C calls, same names
+def hz_strerror(code: int) -> str:
+    return lib().hz_strerror(int(code)).decode()
+
+
+def hz_version() -> int:
+    return int(lib().hz_version())
+
+
+def hz_workspace_bytes(grid: hz_grid, opts: hz_options) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().hz_workspace_bytes(ctypes.byref(grid), ctypes.byref(opts), ctypes.byref(n)),
+           "hz_workspace_bytes")
+    return int(n.value)
+
+
+def hz_create(grid: hz_grid, opts: hz_options, d_workspace: int, nbytes: int, stream: int) -> int:
+    h = ctypes.c_void_p(0)
+    _check(lib().hz_create(ctypes.byref(h), ctypes.byref(grid), ctypes.byref(opts),
+                           ctypes.c_void_p(d_workspace), nbytes, ctypes.c_void_p(stream)), "hz_create")
+    return int(h.value)
+
+
+def hz_destroy(ctx: int) -> None:
+    lib().hz_destroy(ctypes.c_void_p(ctx))
+
+
+def hz_set_metric(ctx: int, d_metric: int) -> None:
+    _check(lib().hz_set_metric(ctypes.c_void_p(ctx), ctypes.c_void_p(d_metric)), "hz_set_metric")
+
+
+def hz_set_primitives(ctx: int, d_prim: int) -> None:
+    _check(lib().hz_set_primitives(ctypes.c_void_p(ctx), ctypes.c_void_p(d_prim)), "hz_set_primitives")
+
+
+def hz_get_primitives(ctx: int, d_prim: int) -> None:
+    _check(lib().hz_get_primitives(ctypes.c_void_p(ctx), ctypes.c_void_p(d_prim)), "hz_get_primitives")
+
+
+def hz_get_conserved(ctx: int, d_cons: int) -> None:
+    _check(lib().hz_get_conserved(ctypes.c_void_p(ctx), ctypes.c_void_p(d_cons)), "hz_get_conserved")
+
+
+def hz_step(ctx: int, dt: float) -> None:
+    _check(lib().hz_step(ctypes.c_void_p(ctx), float(dt)), "hz_step")
+
+
+def hz_step_cfl(ctx: int, cfl: float, t_end: float) -> None:
+    _check(lib().hz_step_cfl(ctypes.c_void_p(ctx), float(cfl), float(t_end)), "hz_step_cfl")
+
+
+def hz_max_speed(ctx: int) -> float:
+    v = ctypes.c_double(0.0)
+    _check(lib().hz_max_speed(ctypes.c_void_p(ctx), ctypes.byref(v)), "hz_max_speed")
+    return float(v.value)
+
+
+def hz_get_stats(ctx: int) -> hz_stats:
+    s = hz_stats()
+    code = lib().hz_get_stats(ctypes.c_void_p(ctx), ctypes.byref(s))
+    if code < 0:
+        raise HznError(code, "hz_get_stats")
+    return s
+
+
+def _check(code: int, call: str) -> int:
+    if code < 0:
+        raise HznError(code, call)
+    return code
+
+
+# ------------------------------------------------------------------ convenience
+def make_grid(n, dx, bc) -> hz_grid:
+    g = hz_grid()
+    for d in range(3):
+        g.n[d], g.dx[d], g.bc[d] = int(n[d]), float(dx[d]), int(bc[d])
+    return g
+
+
+def make_options(gamma: float, precision: int = HZ_FP64, cleaning: bool = False, ch: float = 0.0,
+                 kappa: float = 0.0, rho_floor: float = 1e-12, rho_atm: float = 0.0,
+                 p_floor: float = 1e-14, atm_K: float = 0.0, c2p_maxit: int = 50,
+                 c2p_tol: float = 1e-12) -> hz_options:
+    return hz_options(float(gamma), int(precision), int(bool(cleaning)), float(ch), float(kappa),
+                      float(rho_floor), float(rho_atm), float(p_floor), float(atm_K), int(c2p_maxit),
+                      float(c2p_tol))
+
+
+class Solver:
+    """One grid on the current CUDA device: workspace from torch, calls through the C-ABI."""
+
+    def __init__(self, n, dx, bc, options: hz_options, device: Optional[str] = None, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.n = tuple(int(k) for k in n)
+        self.grid = make_grid(n, dx, bc)
+        self.options = options
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = hz_workspace_bytes(self.grid, options)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.ctx = hz_create(self.grid, options, aligned, nbytes, self.stream.cuda_stream)
+        self.ghost = tuple(1 if k > 1 else 0 for k in self.n)
+
+    @classmethod
+    def for_problem(cls, prob, precision: int = HZ_FP64, c2p_maxit: int = 50, c2p_tol: float = 1e-12,
+                    **kw):
+        opts = make_options(prob.gamma, precision=precision, cleaning=prob.cleaning, ch=prob.ch,
+                            kappa=prob.kappa, rho_floor=prob.rho_floor, rho_atm=prob.rho_atm,
+                            p_floor=prob.p_floor,
+                            atm_K=prob.atm_K, c2p_maxit=c2p_maxit, c2p_tol=c2p_tol)
+        s = cls(prob.n, prob.dx, prob.bc, opts, **kw)
+        s.set_metric(prob.metric)
+        s.set_primitives(prob.prim)
+        return s
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            hz_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a):
+        t = self.torch
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a, dtype=np.float64))
+        a = a.to(device=self.device, dtype=t.float64).contiguous()
+        return a
+
+    def _shape(self):
+        return (9, self.n[2], self.n[1], self.n[0])
+
+    def set_metric(self, metric):
+        m = self._dev(metric)
+        g = self.ghost
+        want = (10, self.n[2] + 2 * g[2], self.n[1] + 2 * g[1], self.n[0] + 2 * g[0])
+        if tuple(m.shape) != want:
+            raise ValueError(f"metric shape {tuple(m.shape)} != {want}")
+        hz_set_metric(self.ctx, m.data_ptr())
+        self._keep = m  # keep alive until the copy has run on the stream
+
+    def set_primitives(self, prim):
+        p = self._dev(prim)
+        if tuple(p.shape) != self._shape():
+            raise ValueError(f"primitive shape {tuple(p.shape)} != {self._shape()}")
+        hz_set_primitives(self.ctx, p.data_ptr())
+        self._keep_p = p
+
+    def step(self, dt: float):
+        hz_step(self.ctx, dt)
+
+    def step_cfl(self, cfl: float, t_end: float):
+        hz_step_cfl(self.ctx, cfl, t_end)
+
+    def max_speed(self) -> float:
+        return hz_max_speed(self.ctx)
+
+    def stats(self) -> hz_stats:
+        return hz_get_stats(self.ctx)
+
+    def primitives(self):
+        out = self.torch.empty(self._shape(), dtype=self.torch.float64, device=self.device)
+        hz_get_primitives(self.ctx, out.data_ptr())
+        return out
+
+    def conserved(self):
+        out = self.torch.empty(self._shape(), dtype=self.torch.float64, device=self.device)
+        hz_get_conserved(self.ctx, out.data_ptr())
+        return out
+
+    def evolve(self, t_end: float, cfl: float, max_steps: int = 1 << 40) -> int:
+        """Advance with device-side CFL steps until t_end; returns the steps taken."""
+        steps = 0
+        while steps < max_steps:
+            s = self.stats()
+            if s.t >= t_end:
+                break
+            self.step_cfl(cfl, t_end)
+            steps += 1
+        return steps

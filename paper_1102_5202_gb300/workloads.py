@@ -51,6 +51,7 @@ class Problem:
     ch: float = 0.0
     kappa: float = 0.0
     rho_floor: float = 1e-12
+    rho_atm: float = 0.0                    # atmosphere threshold on D / sqrt(gamma) (0: off)
     p_floor: float = 1e-14
     atm_K: float = 0.0
     steps: int = 0                          # fixed step count of the benchmark problems
@@ -61,6 +62,18 @@ class Problem:
 
     def ghosts(self) -> Tuple[int, int, int]:
         return tuple(1 if k > 1 else 0 for k in self.n)
+
+    def subbox(self, lo: Sequence[int], hi: Sequence[int], name: str = "") -> "Problem":
+        """Cells lo <= (i, j, k) < hi as a problem of its own: primitives, the metric with its
+        ghost layer, and every option; boundaries stay those of the parent."""
+        g = self.ghosts()
+        prim = np.ascontiguousarray(self.prim[:, lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]])
+        met = np.ascontiguousarray(self.metric[:, lo[2]:hi[2] + 2 * g[2], lo[1]:hi[1] + 2 * g[1],
+                                               lo[0]:hi[0] + 2 * g[0]])
+        x0 = tuple(self.x0[d] + lo[d] * self.dx[d] for d in range(3))
+        n = tuple(int(hi[d] - lo[d]) for d in range(3))
+        return dataclasses.replace(self, name=name or f"{self.name}_sub", n=n, x0=x0, prim=prim,
+                                   metric=met)
 
 
 def metric_ghosts(n: Sequence[int]) -> Tuple[int, int, int]:
@@ -235,7 +248,8 @@ def blob3d(n: int = 192, seed: int = 1102, half_width: float = 20.0, kappa: floa
     return Problem(name=f"blob3d_{n}", n=nn, dx=(dx,) * 3, x0=x0, bc=(0, 0, 0),
                    gamma=BLOB_GAMMA, prim=np.ascontiguousarray(prim), metric=met,
                    t_end=0.0, cfl=0.5, cleaning=cleaning, ch=ch, kappa=kappa,
-                   rho_floor=1e-11 * BLOB_RHOC, p_floor=1e-30, atm_K=BLOB_K, steps=steps)
+                   rho_floor=BLOB_ATM * BLOB_RHOC, rho_atm=10.0 * BLOB_ATM * BLOB_RHOC,
+                   p_floor=1e-30, atm_K=BLOB_K, steps=steps)
 
 
 # ------------------------------------------------------------------ ensemble of 1-D tubes

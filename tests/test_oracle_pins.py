@@ -29,7 +29,7 @@ GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "go
 def _setup(P, **kw):
     grid = O.make_grid(P.n, P.dx, P.bc)
     opts = O.make_opts(P.gamma, cleaning=P.cleaning, ch=P.ch, kappa=P.kappa,
-                       rho_floor=P.rho_floor, p_floor=P.p_floor, atm_K=P.atm_K, **kw)
+                       rho_floor=P.rho_floor, p_floor=P.p_floor, atm_K=P.atm_K, rho_atm=P.rho_atm, **kw)
     return grid, opts
 
 
