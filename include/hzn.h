@@ -45,7 +45,8 @@ enum {
   HZ_ERR_CUDA = -2,      /* a CUDA runtime call failed (the context may be unusable)     */
   HZ_ERR_STATE = -3,     /* call out of order (e.g. step before metric and primitives)   */
   HZ_ERR_WORKSPACE = -4, /* workspace pointer misaligned or smaller than required        */
-  HZ_ERR_UNSUPPORTED = -5/* option combination not built                                 */
+  HZ_ERR_UNSUPPORTED = -5,/* option combination not built                                */
+  HZ_ERR_TOO_LARGE = -6  /* grid needs more than HZ_NOALLOC_SCRATCH_BYTES (hz_step_noalloc) */
 };
 
 enum { HZ_BC_OUTFLOW = 0, HZ_BC_PERIODIC = 1 };
@@ -135,6 +136,36 @@ const char* hz_strerror(int code);
 
 /* HZN_VERSION of the loaded library. */
 int hz_version(void);
+
+/* ---- Whole update without allocation --------------------------------------------------
+ * The paper has no counterpart to this call; it is a convenience of this library.
+ *
+ * hz_create needs a caller-provided device workspace.  Some callers cannot allocate one: a
+ * solver embedded as a plug-in in a host framework that owns all device memory through its
+ * own pool and does not let plug-ins call cudaMalloc (an allocation outside the pool breaks
+ * its accounting or fragments it), or a thin foreign-function layer that can only pass
+ * pointers it was given.  hz_step_noalloc serves them: it takes the metric, the primitive
+ * state in and a buffer for the primitive state out, advances nsteps RK3 steps of fixed size
+ * dt (nsteps = 0 only converts to conserved and back), and writes the result.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine, on the device or the host.
+ *
+ * Its scratch (the workspace hz_create would take) is one static device array of
+ * HZ_NOALLOC_SCRATCH_BYTES (16 MiB) inside libhzn.so; every GPU that loads the library holds
+ * it until the process exits.  A grid whose hz_workspace_bytes exceeds that size is rejected
+ * with HZ_ERR_TOO_LARGE (for example 32^3 cells fit, 64^3 do not).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array and leaves its own state in it; each call overwrites
+ *     everything it reads (and clears its counters) before use.  Calls whose GPU work
+ *     overlaps (two streams, or two host threads) race on the array and give wrong results:
+ *     serialise them.
+ *   - Arguments and layouts are those of hz_set_metric / hz_set_primitives /
+ *     hz_get_primitives; all work is enqueued on stream.  No statistics are returned. */
+#define HZ_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hz_step_noalloc(const hz_grid* grid, const hz_options* opts, const double* d_metric,
+                    const double* d_prim_in, double* d_prim_out, double dt, int nsteps,
+                    void* stream);
 
 #ifdef __cplusplus
 }

@@ -668,43 +668,11 @@ int run_step(hz_ctx* c, int mode, double dt, double cfl, double t_end) {
   return cuda_err(cudaGetLastError());
 }
 
-}  // namespace
-
-extern "C" {
-
-int hz_version(void) { return HZN_VERSION; }
-
-const char* hz_strerror(int code) {
-  switch (code) {
-    case HZ_OK: return "ok";
-    case HZ_WARN_C2P: return "completed; some cells were reset to atmosphere by the recovery";
-    case HZ_ERR_ARG: return "invalid argument";
-    case HZ_ERR_CUDA: return "CUDA runtime error";
-    case HZ_ERR_STATE: return "call out of order (metric and primitives must be set first)";
-    case HZ_ERR_WORKSPACE: return "workspace misaligned or too small";
-    case HZ_ERR_UNSUPPORTED: return "option combination not supported";
-    default: return "unknown code";
-  }
-}
-
-int hz_workspace_bytes(const hz_grid* grid, const hz_options* opts, size_t* bytes) {
-  if (!bytes) return HZ_ERR_ARG;
-  const int e = check_args(grid, opts);
-  if (e != HZ_OK) return e;
-  *bytes = layout_of(grid).total;
-  return HZ_OK;
-}
-
-int hz_create(hz_ctx** ctx, const hz_grid* grid, const hz_options* opts, void* d_workspace,
-              size_t bytes, void* stream) {
-  if (!ctx) return HZ_ERR_ARG;
-  *ctx = nullptr;
-  int e = check_args(grid, opts);
-  if (e != HZ_OK) return e;
+// Fill a context for a checked grid and options over a workspace of at least layout_of().total
+// bytes, and clear the device scalars on the stream.
+int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_workspace,
+             size_t bytes, void* stream) {
   const Layout L = layout_of(grid);
-  if (!d_workspace || ((uintptr_t)d_workspace & 255u) != 0 || bytes < L.total) return HZ_ERR_WORKSPACE;
-  hz_ctx* c = new (std::nothrow) hz_ctx;
-  if (!c) return HZ_ERR_ARG;
   memset(c, 0, sizeof(*c));
   c->g = *grid;
   c->o = *opts;
@@ -767,7 +735,48 @@ int hz_create(hz_ctx** ctx, const hz_grid* grid, const hz_options* opts, void* d
   c->grid3 = dim3(1, 1, (kp.nz + kp.zlen - 1) / kp.zlen);
 
   k_reset_scalars<<<1, 1, 0, c->st>>>(c->sc);
-  e = cuda_err(cudaGetLastError());
+  return cuda_err(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+int hz_version(void) { return HZN_VERSION; }
+
+const char* hz_strerror(int code) {
+  switch (code) {
+    case HZ_OK: return "ok";
+    case HZ_WARN_C2P: return "completed; some cells were reset to atmosphere by the recovery";
+    case HZ_ERR_ARG: return "invalid argument";
+    case HZ_ERR_CUDA: return "CUDA runtime error";
+    case HZ_ERR_STATE: return "call out of order (metric and primitives must be set first)";
+    case HZ_ERR_WORKSPACE: return "workspace misaligned or too small";
+    case HZ_ERR_UNSUPPORTED: return "option combination not supported";
+    case HZ_ERR_TOO_LARGE: return "grid too large for the fixed scratch of hz_step_noalloc";
+    default: return "unknown code";
+  }
+}
+
+int hz_workspace_bytes(const hz_grid* grid, const hz_options* opts, size_t* bytes) {
+  if (!bytes) return HZ_ERR_ARG;
+  const int e = check_args(grid, opts);
+  if (e != HZ_OK) return e;
+  *bytes = layout_of(grid).total;
+  return HZ_OK;
+}
+
+int hz_create(hz_ctx** ctx, const hz_grid* grid, const hz_options* opts, void* d_workspace,
+              size_t bytes, void* stream) {
+  if (!ctx) return HZ_ERR_ARG;
+  *ctx = nullptr;
+  int e = check_args(grid, opts);
+  if (e != HZ_OK) return e;
+  const Layout L = layout_of(grid);
+  if (!d_workspace || ((uintptr_t)d_workspace & 255u) != 0 || bytes < L.total) return HZ_ERR_WORKSPACE;
+  hz_ctx* c = new (std::nothrow) hz_ctx;
+  if (!c) return HZ_ERR_ARG;
+  e = ctx_init(c, grid, opts, d_workspace, bytes, stream);
   if (e != HZ_OK) {
     delete c;
     return e;
@@ -868,3 +877,61 @@ int hz_get_stats(hz_ctx* c, hz_stats* h_out) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------------------
+// Whole update without any allocation (hz_step_noalloc).  The scratch that hz_create would
+// take from the caller's workspace lives in one file-scope device array instead.  Host code
+// may not use the array's name as an address: the device address is looked up once per
+// device with cudaGetSymbolAddress and passed to the kernels as a pointer.
+// ----------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = HZ_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoallocMaxDevices];  // device address of g_noalloc_scratch, per device
+
+// Device address of the scratch array on the current device (looked up on first use).
+int noalloc_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HZ_ERR_CUDA;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return HZ_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HZ_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HZ_OK;
+}
+
+}  // namespace
+
+extern "C" int hz_step_noalloc(const hz_grid* grid, const hz_options* opts, const double* d_metric,
+                               const double* d_prim_in, double* d_prim_out, double dt, int nsteps,
+                               void* stream) {
+  if (!d_metric || !d_prim_in || !d_prim_out || nsteps < 0 || (nsteps > 0 && !(dt > 0.0)))
+    return HZ_ERR_ARG;
+  int e = check_args(grid, opts);
+  if (e != HZ_OK) return e;
+  if (layout_of(grid).total > kNoallocScratchBytes) return HZ_ERR_TOO_LARGE;
+  void* scratch = nullptr;
+  e = noalloc_scratch(&scratch);
+  if (e != HZ_OK) return e;
+  hz_ctx c;  // host bookkeeping on the stack: nothing is allocated on the host either
+  e = ctx_init(&c, grid, opts, scratch, kNoallocScratchBytes, stream);
+  if (e != HZ_OK) return e;
+  // every call overwrites the whole state it reads: metric, primitives, conserved state and
+  // the counters (cleared by hz_set_primitives) start from this call's inputs
+  if ((e = hz_set_metric(&c, d_metric)) != HZ_OK) return e;
+  if ((e = hz_set_primitives(&c, d_prim_in)) != HZ_OK) return e;
+  for (int s = 0; s < nsteps; ++s)
+    if ((e = hz_step(&c, dt)) != HZ_OK) return e;
+  return hz_get_primitives(&c, d_prim_out);
+}

@@ -21,13 +21,15 @@ from . import build as _build
 
 HZ_OK, HZ_WARN_C2P = 0, 1
 HZ_ERR_ARG, HZ_ERR_CUDA, HZ_ERR_STATE, HZ_ERR_WORKSPACE, HZ_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
+HZ_ERR_TOO_LARGE = -6
+HZ_NOALLOC_SCRATCH_BYTES = 16 << 20
 HZ_BC_OUTFLOW, HZ_BC_PERIODIC = 0, 1
 HZ_FP64, HZ_MIXED = 0, 1
 
 EXPORTED = (
     "hz_workspace_bytes", "hz_create", "hz_destroy", "hz_set_metric", "hz_set_primitives",
     "hz_get_primitives", "hz_get_conserved", "hz_step", "hz_step_cfl", "hz_max_speed",
-    "hz_get_stats", "hz_strerror", "hz_version",
+    "hz_get_stats", "hz_strerror", "hz_version", "hz_step_noalloc",
 )
 
 
@@ -98,6 +100,8 @@ def lib():
             L.hz_step_cfl.argtypes = [vp, ctypes.c_double, ctypes.c_double]
             L.hz_max_speed.argtypes = [vp, dp]
             L.hz_get_stats.argtypes = [vp, P(hz_stats)]
+            L.hz_step_noalloc.argtypes = [P(hz_grid), P(hz_options), vp, vp, vp, ctypes.c_double,
+                                          ctypes.c_int, vp]
             L.hz_strerror.argtypes = [ctypes.c_int]
             L.hz_strerror.restype = ctypes.c_char_p
             L.hz_version.restype = ctypes.c_int
@@ -171,6 +175,14 @@ def hz_get_stats(ctx: int) -> hz_stats:
     if code < 0:
         raise HznError(code, "hz_get_stats")
     return s
+
+
+def hz_step_noalloc(grid: hz_grid, opts: hz_options, d_metric: int, d_prim_in: int, d_prim_out: int,
+                    dt: float, nsteps: int, stream: int) -> None:
+    """nsteps fixed-dt RK3 steps with the library's static scratch (no allocation at all)."""
+    _check(lib().hz_step_noalloc(ctypes.byref(grid), ctypes.byref(opts), ctypes.c_void_p(d_metric),
+                                 ctypes.c_void_p(d_prim_in), ctypes.c_void_p(d_prim_out), float(dt),
+                                 int(nsteps), ctypes.c_void_p(stream)), "hz_step_noalloc")
 
 
 def _check(code: int, call: str) -> int:
