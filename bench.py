@@ -40,13 +40,20 @@ FP64_PEAK_TFLOPS = 1.194
 # FP64 operations per cell per substep executed by the fused substep kernel (3-D, cleaning
 # on), from ncu instruction counters on the 128^3 blob (profiles/k_substep_blob3d.md):
 # DFMA counted as 2 flops, DADD/DMUL as 1.
-FP64_FLOPS_PER_CELL_SUBSTEP = 3638.8
+FP64_FLOPS_PER_CELL_SUBSTEP = 2547.9
 # DRAM bytes per cell per substep of the same kernel from the same capture (read + write,
-# 822.3 MB per launch at 128^3), scaled to a full launch by the cell count.
-DRAM_BYTES_PER_CELL_SUBSTEP = 392.1
+# 683.8 MB per launch at 128^3), scaled to a full launch by the cell count.
+DRAM_BYTES_PER_CELL_SUBSTEP = 326.1
+# The same two figures for the mixed-precision substep kernel (profiles/k_substep_mixed_blob3d.md):
+# FP64 flops (recovery, update) per cell per substep, and DRAM bytes per cell per substep.
+MIXED_FP64_FLOPS_PER_CELL_SUBSTEP = 202.2
+MIXED_DRAM_BYTES_PER_CELL_SUBSTEP = None
 # Algorithmic HBM bytes per zone update (three substeps, FP64, nine fields): read P, U_k, U0,
 # metric and write U_{k+1}, P_{k+1} once per substep; stage 1 reads U0 once.
 HBM_BYTES_PER_ZU = (46 + 55 + 55) * 8
+# Mixed precision: primitives and metric stored in FP32 (4 B), conserved state in FP64 (8 B):
+# stage 1 reads P, metric, U0 and writes U, P; stages 2-3 also read U_k.
+HBM_BYTES_PER_ZU_MIXED = (9 * 4 + 10 * 4 + 9 * 8 + 9 * 8 + 9 * 4) + 2 * (9 * 4 + 10 * 4 + 2 * 9 * 8 + 9 * 8 + 9 * 4)
 
 
 def parse():
@@ -58,6 +65,8 @@ def parse():
     ap.add_argument("--n", type=int, default=192, help="cells per axis of the blob")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--n-mixed", type=int, default=384, help="cells per axis of the mixed line")
     return ap.parse_args()
 
 
@@ -211,6 +220,12 @@ def run_gpu(args, rank, world, local):
     if not args.no_e2e:
         e2e = run_e2e(s, P, args, dist, local)
 
+    mixed = None
+    if not args.no_mixed:
+        del s
+        torch.cuda.empty_cache()
+        mixed = run_mixed(args, dist, local, hbm_peak)
+
     line = None
     if rank == 0:
         cpu = None
@@ -228,6 +243,7 @@ def run_gpu(args, rank, world, local):
             "hbm_roofline": hbm,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "mixed": mixed,
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "c2p_failures": int(st.c2p_failures),
@@ -238,6 +254,55 @@ def run_gpu(args, rank, world, local):
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def run_mixed(args, dist, local, hbm_peak):
+    """The mixed-precision configuration: the same blob at 384^3 (FP32 faces and sources,
+    FP64 conserved state, update, recovery and CFL), timed like the FP64 line."""
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+    from paper_1102_5202_gb300 import workloads as W
+
+    P = W.blob3d(args.n_mixed)
+    s = hzn.Solver.for_problem(P, precision=hzn.HZ_MIXED)
+    for _ in range(args.warmup):
+        s.step_cfl(0.5, 1e30)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s.stream):
+        a.record(s.stream)
+        for _ in range(args.steps):
+            s.step_cfl(0.5, 1e30)
+        b.record(s.stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) * 1e-3
+    st = s.stats()
+    units, seconds = aggregate(float(P.ncell) * args.steps, sec, dist, device=torch.device("cuda", local))
+    value = units / seconds
+    ach = HBM_BYTES_PER_ZU_MIXED * value / world_size(dist) / 1e9
+    substep_s = sec / args.steps / 3.0
+    fl = MIXED_FP64_FLOPS_PER_CELL_SUBSTEP * P.ncell / substep_s / 1e12
+    del s
+    torch.cuda.empty_cache()
+    return {"value": value, "unit": UNIT, "workload": f"blob3d_{args.n_mixed}^3_mixed_cleaning",
+            "cells": P.ncell, "ms_per_step": seconds / args.steps * 1e3, "dtype": "f32/f64",
+            "roofline": {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": fl / FP64_PEAK_TFLOPS,
+                         "traffic": (MIXED_DRAM_BYTES_PER_CELL_SUBSTEP * P.ncell
+                                     if MIXED_DRAM_BYTES_PER_CELL_SUBSTEP else None),
+                         "kernel": "k_substep<32,4,3-D,cleaning,diag,mixed> (FP64 recovery and update)"},
+            "hbm_roofline": {"bytes_per_zu": HBM_BYTES_PER_ZU_MIXED, "achieved": ach, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": ach / hbm_peak,
+                             "roofline_zu_per_s": hbm_peak * 1e9 / HBM_BYTES_PER_ZU_MIXED},
+            "c2p_failures": int(st.c2p_failures), "gpu_launches": 4 * args.steps}
+
+
+def world_size(dist):
+    return 1 if dist is None else dist.get_world_size()
 
 
 def run_e2e(s, P, args, dist, local):

@@ -66,7 +66,10 @@ typedef struct {
 /* Physics and numerics options (§3.2 lists the scheme choices; the values are run inputs). */
 typedef struct {
   double gamma;     /* ideal-gas index, p = (gamma - 1) rho eps; 1 < gamma <= 3          */
-  int precision;    /* HZ_FP64 (every step in FP64) | HZ_MIXED (reserved)                   */
+  int precision;    /* HZ_FP64: every step in FP64.  HZ_MIXED: primitives and metric stored
+                       in FP32; reconstruction, HLLE fluxes and sources in FP32 with the flux
+                       divergence accumulated in FP32; the conserved state (stored in FP64),
+                       its RK update, the recovery and the CFL maximum in FP64 (§3.2, §6)  */
   int cleaning;     /* 1: hyperbolic divergence cleaning with the field psi (§3.2)         */
   double ch;        /* cleaning speed as a fraction of light speed (0 < ch <= 1)          */
   double kappa;     /* cleaning damping rate (>= 0)                                       */
@@ -103,7 +106,9 @@ int hz_create(hz_ctx** ctx, const hz_grid* grid, const hz_options* opts, void* d
 int hz_destroy(hz_ctx* ctx);
 
 /* Copy the metric at cell centres, ghost layer included (10 x Nm doubles, layout above) into
- * the workspace.  The metric is the fixed spacetime of §2.1 (Cowling approximation). */
+ * the workspace.  The metric is the fixed spacetime of §2.1 (Cowling approximation).  The copy
+ * also checks whether the shift and the off-diagonal gamma_ij vanish everywhere; if they do,
+ * the kernels drop those identically zero terms.  Synchronises the stream. */
 int hz_set_metric(hz_ctx* ctx, const double* d_metric);
 
 /* Copy the primitive state (9 x N doubles) into the workspace and compute the conserved

@@ -1,0 +1,51 @@
+// Dispatch of the kernel launchers on dimensionality and precision.
+#include "hzn_kernels.cuh"
+
+namespace hzn {
+
+#define HZN_DECLARE(P, D)                                                                          \
+  void launch_substep_k##P##_##D##d(const Variant&, const KParams&, const StageArgs&, const void*, \
+                                    DevScalars*, int, cudaStream_t);                               \
+  void launch_max_speed_k##P##_##D##d(const Variant&, const KParams&, const void*, const void*,    \
+                                      DevScalars*, cudaStream_t);
+HZN_DECLARE(64, 1)
+HZN_DECLARE(64, 2)
+HZN_DECLARE(64, 3)
+HZN_DECLARE(32, 1)
+HZN_DECLARE(32, 2)
+HZN_DECLARE(32, 3)
+#undef HZN_DECLARE
+
+void launch_substep(const Variant& v, const KParams& kp, const StageArgs& sa, const void* M,
+                    DevScalars* sc, int zchunks, cudaStream_t st) {
+  if (v.mixed) {
+    if (v.dims == 1) launch_substep_k32_1d(v, kp, sa, M, sc, zchunks, st);
+    else if (v.dims == 2) launch_substep_k32_2d(v, kp, sa, M, sc, zchunks, st);
+    else launch_substep_k32_3d(v, kp, sa, M, sc, zchunks, st);
+  } else {
+    if (v.dims == 1) launch_substep_k64_1d(v, kp, sa, M, sc, zchunks, st);
+    else if (v.dims == 2) launch_substep_k64_2d(v, kp, sa, M, sc, zchunks, st);
+    else launch_substep_k64_3d(v, kp, sa, M, sc, zchunks, st);
+  }
+}
+
+void launch_max_speed(const Variant& v, const KParams& kp, const void* P, const void* M,
+                      DevScalars* sc, cudaStream_t st) {
+  if (v.mixed) {
+    if (v.dims == 1) launch_max_speed_k32_1d(v, kp, P, M, sc, st);
+    else if (v.dims == 2) launch_max_speed_k32_2d(v, kp, P, M, sc, st);
+    else launch_max_speed_k32_3d(v, kp, P, M, sc, st);
+  } else {
+    if (v.dims == 1) launch_max_speed_k64_1d(v, kp, P, M, sc, st);
+    else if (v.dims == 2) launch_max_speed_k64_2d(v, kp, P, M, sc, st);
+    else launch_max_speed_k64_3d(v, kp, P, M, sc, st);
+  }
+}
+
+void launch_prim2cons(const Variant& v, const KParams& kp, const void* P, const void* M, double* U,
+                      cudaStream_t st) {
+  if (v.mixed) launch_prim2cons_t<true>(v, kp, P, M, U, st);
+  else launch_prim2cons_t<false>(v, kp, P, M, U, st);
+}
+
+}  // namespace hzn

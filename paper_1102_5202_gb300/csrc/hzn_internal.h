@@ -1,0 +1,71 @@
+// hzn_internal.h -- structures shared by the host API and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hzn {
+
+// Device-resident scalars: the time-step clock and the run statistics.
+struct DevScalars {
+  unsigned long long vmax_bits;  // max speed / dx of the newest state (bits of a positive double)
+  unsigned long long fails;      // recovery failures since hz_set_primitives
+  int maxit;                     // largest Newton iteration count
+  unsigned int metric_general;   // set by the metric scan: nonzero shift or off-diagonal gamma
+  double dt;                     // dt of the step in flight
+  double t;                      // simulated time
+  long long steps;
+};
+
+struct KParams {
+  int nx, ny, nz;
+  int bcx, bcy, bcz;
+  int pitch;             // x pitch of the interior arrays
+  long long plane;       // pitch * ny
+  long long fs;          // field stride of the interior arrays
+  int mpitch, mny;       // metric x pitch, metric y extent
+  long long mplane;      // mpitch * mny
+  long long ms;          // metric field stride
+  int gx, gy, gz;        // metric ghost widths
+  double idx, idy, idz;  // 1 / dx
+  double gamma, gfac, ch, kappa;
+  double rho_floor, rho_atm, p_floor, p_atm;
+  int c2p_maxit;
+  double c2p_tol;
+  int zlen;              // cells of z per block
+};
+
+// One substep: Uout = a0 U0 + ak (Uk + dt L(Pin)); Pout = primitives of Uout.
+struct StageArgs {
+  const void* Pin;       // primitive state (double, or float in the mixed path)
+  void* Pout;
+  const double* U0;
+  const double* Uk;
+  double* Uout;
+  double a0, ak;
+  int last;              // 1 on the last substep: accumulate the CFL maximum
+};
+
+// Which instantiation to launch.
+struct Variant {
+  int dims;    // 1, 2 or 3 active axes (x, then y, then z)
+  int clean;   // divergence cleaning
+  int diag;    // zero shift and diagonal gamma everywhere
+  int mixed;   // FP32 storage of P and metric, FP32 faces/sources
+};
+
+// Launchers, one per (precision, dims) translation unit; dispatch in hzn_dispatch.cu.
+void launch_substep(const Variant& v, const KParams& kp, const StageArgs& sa, const void* M,
+                    DevScalars* sc, int zchunks, cudaStream_t st);
+void launch_prim2cons(const Variant& v, const KParams& kp, const void* P, const void* M, double* U,
+                      cudaStream_t st);
+void launch_max_speed(const Variant& v, const KParams& kp, const void* P, const void* M,
+                      DevScalars* sc, cudaStream_t st);
+
+// Tile shape of the substep kernel per dimensionality.
+inline void tile_of(int dims, int* tx, int* ty) {
+  *tx = dims == 1 ? 128 : 32;
+  *ty = dims == 1 ? 1 : 4;
+}
+
+}  // namespace hzn

@@ -1,0 +1,577 @@
+// hzn_kernels.cuh -- the fused finite-volume substep kernel and its helpers (templates).
+//
+// One launch performs one Runge-Kutta substep (§3.2) for every cell: MC reconstruction of the
+// primitive state to the faces, face metric, HLLE flux (§2.2), flux divergence and metric
+// source (§2.1 Eq. 2), the RK stage combination, the Newton recovery of the new primitive
+// state (§2.2) and, after the last substep, the maximum characteristic speed for the next
+// time step (a warp-shuffle / atomic max).  Paper prior art (§3.3): thread blocks of 32 cells
+// along x marching in z, padded rows; here a block owns a TX x TY column tile and a chunk of z,
+// keeps the face fluxes of a plane in shared memory, reuses each z-face between two planes,
+// and computes every face exactly once per tile.
+//
+// Precision (§3.2 lists SP, DP and DP-only recovery; §6 adjustable flux-difference precision):
+//   FP64 path   every step in double;
+//   mixed path  primitives and metric stored in float; reconstruction, face fluxes, HLLE and
+//               sources in float with the flux divergence accumulated in float; the RK update
+//               of the conserved state (stored in double), the recovery and the CFL maximum
+//               in double.
+//
+// Grid storage: structure of arrays, x fastest, rows padded to 16 elements; the metric carries
+// its ghost layer; primitive boundaries are applied as clamped (outflow) or wrapped (periodic)
+// indices, so no primitive ghosts are stored.
+#pragma once
+
+#include "hzn_internal.h"
+#include "hzn_physics.cuh"
+
+namespace hzn {
+
+template <bool MIXED>
+struct Prec;
+template <>
+struct Prec<false> {
+  using R = double;  // face / source arithmetic
+  using S = double;  // storage of primitives and metric
+};
+template <>
+struct Prec<true> {
+  using R = float;
+  using S = float;
+};
+
+__device__ __forceinline__ int bc_index(int q, int n, int periodic) {
+  if (periodic) {
+    q = q < 0 ? q + n : q;
+    q = q >= n ? q - n : q;
+    return q;
+  }
+  return q < 0 ? 0 : (q >= n ? n - 1 : q);
+}
+
+__device__ __forceinline__ long long met_off(const KParams& kp, int i, int j, int k) {
+  return (long long)(k + kp.gz) * kp.mplane + (long long)(j + kp.gy) * kp.mpitch + (i + kp.gx);
+}
+
+template <typename R>
+__device__ __forceinline__ Consts<R> consts_of(const KParams& kp) {
+  Consts<R> c;
+  c.gamma = (R)kp.gamma;
+  c.gfac = (R)kp.gfac;
+  c.ch = (R)kp.ch;
+  c.ch2 = (R)(kp.ch * kp.ch);
+  return c;
+}
+
+// The ten metric values at one cell (only alpha and the diagonal for DIAG).
+template <bool DIAG, typename R, typename S>
+__device__ __forceinline__ void load_metric(const KParams& kp, const S* __restrict__ M, long long off,
+                                            R m[10]) {
+  if constexpr (DIAG) {
+    m[M_ALP] = (R)__ldg(M + M_ALP * kp.ms + off);
+    m[M_GXX] = (R)__ldg(M + M_GXX * kp.ms + off);
+    m[M_GYY] = (R)__ldg(M + M_GYY * kp.ms + off);
+    m[M_GZZ] = (R)__ldg(M + M_GZZ * kp.ms + off);
+    m[M_BX] = m[M_BY] = m[M_BZ] = m[M_GXY] = m[M_GXZ] = m[M_GYZ] = R(0);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 10; ++f) m[f] = (R)__ldg(M + f * kp.ms + off);
+  }
+}
+
+// HLLE flux of the face at i - 1/2 along D of cell (i, j, k) (the face between cells i-1 and
+// i along D), written to out[f * ostride].
+template <int D, bool CLEAN, bool DIAG, typename R, typename S>
+__device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict__ P,
+                                          const S* __restrict__ M, int i, int j, int k, R* out,
+                                          int ostride) {
+  constexpr int NV = CLEAN ? 9 : 8;
+  long long off[4];  // stencil cells s = -2 .. 1 along D
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    int ii = i, jj = j, kk = k;
+    if (D == 0) ii = bc_index(i + s - 2, kp.nx, kp.bcx);
+    if (D == 1) jj = bc_index(j + s - 2, kp.ny, kp.bcy);
+    if (D == 2) kk = bc_index(k + s - 2, kp.nz, kp.bcz);
+    off[s] = (long long)kk * kp.plane + (long long)jj * kp.pitch + ii;
+  }
+  R PL[9], PR[9];
+#pragma unroll
+  for (int f = 0; f < NV; ++f) {
+    const S* pf = P + f * kp.fs;
+    const R a = (R)__ldg(pf + off[0]), b = (R)__ldg(pf + off[1]);
+    const R cc = (R)__ldg(pf + off[2]), d = (R)__ldg(pf + off[3]);
+    const R d0 = b - a, d1 = cc - b, d2 = d - cc;
+    PL[f] = b + mc_half_slope(d0, d1);
+    PR[f] = cc - mc_half_slope(d1, d2);
+  }
+  if (!CLEAN) PL[8] = PR[8] = R(0);
+  // face metric: mean of the two adjacent centre values
+  R m[10];
+  {
+    const long long o1 = met_off(kp, i, j, k);
+    const long long o0 = o1 - (D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane));
+    R m0[10], m1[10];
+    load_metric<DIAG>(kp, M, o0, m0);
+    load_metric<DIAG>(kp, M, o1, m1);
+#pragma unroll
+    for (int f = 0; f < 10; ++f) m[f] = R(0.5) * (m0[f] + m1[f]);
+  }
+  const Geom<R> G = make_geom<DIAG>(m);
+  const Consts<R> c = consts_of<R>(kp);
+  R FL[9], UL[9], lmL, lpL;
+  {
+    const State<R> St = make_state<DIAG>(G, PL, c);
+    flux_of<D, CLEAN, DIAG>(G, St, c, FL);
+    cons_of<CLEAN>(G, St, UL);
+    speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmL, lpL);
+  }
+  R FR[9], UR[9], lmR, lpR;
+  {
+    const State<R> St = make_state<DIAG>(G, PR, c);
+    flux_of<D, CLEAN, DIAG>(G, St, c, FR);
+    cons_of<CLEAN>(G, St, UR);
+    speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmR, lpR);
+  }
+  // HLLE: F = (sR FL - sL FR + sL sR (UR - UL)) / (sR - sL)
+  const R sl = fmin(R(0), fmin(lmL, lmR));
+  const R sr = fmax(R(0), fmax(lpL, lpR));
+  const R den = sr - sl;
+  R wl, wr, wu;
+  if (den != R(0)) {
+    const R iden = R(1) / den;
+    wl = sr * iden;
+    wr = -sl * iden;
+    wu = sl * sr * iden;
+  } else {
+    wl = wr = R(0.5);
+    wu = R(0);
+  }
+#pragma unroll
+  for (int f = 0; f < NV; ++f) out[f * ostride] = wl * FL[f] + (wr * FR[f] + wu * (UR[f] - UL[f]));
+  if (CLEAN) {
+    R cm, cp;
+    clean_speeds<D, DIAG>(G, c.ch, cm, cp);
+    const R csl = fmin(R(0), cm), csr = fmax(R(0), cp);
+    const R cden = csr - csl;
+    const int fb = U_BX + D;
+    if (cden != R(0)) {
+      const R ic = R(1) / cden;
+      out[fb * ostride] = (csr * FL[fb] - csl * FR[fb] + csl * csr * (UR[fb] - UL[fb])) * ic;
+      out[U_PSI * ostride] = (csr * FL[U_PSI] - csl * FR[U_PSI] + csl * csr * (UR[U_PSI] - UL[U_PSI])) * ic;
+    }
+  }
+}
+
+// Centre 4-metric quantities used by the source: g_tt, beta_i, gamma_ij at one cell.
+template <typename R>
+struct G4 {
+  R gtt, blx, bly, blz, gxx, gxy, gxz, gyy, gyz, gzz;
+};
+
+template <bool DIAG, typename R, typename S>
+__device__ __forceinline__ G4<R> g4_at(const KParams& kp, const S* __restrict__ M, long long off) {
+  R m[10];
+  load_metric<DIAG>(kp, M, off, m);
+  G4<R> g;
+  g.gxx = m[M_GXX];
+  g.gyy = m[M_GYY];
+  g.gzz = m[M_GZZ];
+  if constexpr (DIAG) {
+    g.gxy = g.gxz = g.gyz = g.blx = g.bly = g.blz = R(0);
+    g.gtt = -m[M_ALP] * m[M_ALP];
+  } else {
+    g.gxy = m[M_GXY];
+    g.gxz = m[M_GXZ];
+    g.gyz = m[M_GYZ];
+    g.blx = g.gxx * m[M_BX] + g.gxy * m[M_BY] + g.gxz * m[M_BZ];
+    g.bly = g.gxy * m[M_BX] + g.gyy * m[M_BY] + g.gyz * m[M_BZ];
+    g.blz = g.gxz * m[M_BX] + g.gyz * m[M_BY] + g.gzz * m[M_BZ];
+    g.gtt = -m[M_ALP] * m[M_ALP] + (g.blx * m[M_BX] + g.bly * m[M_BY] + g.blz * m[M_BZ]);
+  }
+  return g;
+}
+
+// Contravariant stress-energy T^{ab} = (w + b^2) u^a u^b + (p + b^2/2) g^{ab} - b^a b^b.
+template <typename R>
+struct Tup {
+  R tt, tx, ty, tz, xx, xy, xz, yy, yz, zz;
+};
+
+template <bool DIAG, typename R>
+__device__ __forceinline__ Tup<R> tup_of(const Geom<R>& G, const State<R>& S) {
+  const R wt = S.w + S.b2, pt = S.p + R(0.5) * S.b2;
+  const R ia2 = G.ialp * G.ialp;
+  Tup<R> T;
+  T.tt = wt * S.ut * S.ut - pt * ia2 - S.bt * S.bt;
+  if constexpr (DIAG) {
+    T.tx = wt * S.ut * S.ux - S.bt * S.bx;
+    T.ty = wt * S.ut * S.uy - S.bt * S.by;
+    T.tz = wt * S.ut * S.uz - S.bt * S.bz;
+    T.xx = wt * S.ux * S.ux + pt * G.ixx - S.bx * S.bx;
+    T.yy = wt * S.uy * S.uy + pt * G.iyy - S.by * S.by;
+    T.zz = wt * S.uz * S.uz + pt * G.izz - S.bz * S.bz;
+    T.xy = T.xz = T.yz = R(0);  // multiplied by identically zero metric derivatives
+  } else {
+    T.tx = wt * S.ut * S.ux + pt * G.bx * ia2 - S.bt * S.bx;
+    T.ty = wt * S.ut * S.uy + pt * G.by * ia2 - S.bt * S.by;
+    T.tz = wt * S.ut * S.uz + pt * G.bz * ia2 - S.bt * S.bz;
+    T.xx = wt * S.ux * S.ux + pt * (G.ixx - G.bx * G.bx * ia2) - S.bx * S.bx;
+    T.xy = wt * S.ux * S.uy + pt * (G.ixy - G.bx * G.by * ia2) - S.bx * S.by;
+    T.xz = wt * S.ux * S.uz + pt * (G.ixz - G.bx * G.bz * ia2) - S.bx * S.bz;
+    T.yy = wt * S.uy * S.uy + pt * (G.iyy - G.by * G.by * ia2) - S.by * S.by;
+    T.yz = wt * S.uy * S.uz + pt * (G.iyz - G.by * G.bz * ia2) - S.by * S.bz;
+    T.zz = wt * S.uz * S.uz + pt * (G.izz - G.bz * G.bz * ia2) - S.bz * S.bz;
+  }
+  return T;
+}
+
+// T^{ab} (g_ab(+) - g_ab(-)) between the neighbours gp and gm (unscaled centred difference).
+template <bool DIAG, typename R>
+__device__ __forceinline__ R tdg(const Tup<R>& T, const G4<R>& gp, const G4<R>& gm) {
+  R s = T.tt * (gp.gtt - gm.gtt) + T.xx * (gp.gxx - gm.gxx) + T.yy * (gp.gyy - gm.gyy) +
+        T.zz * (gp.gzz - gm.gzz);
+  if constexpr (!DIAG)
+    s += R(2) * (T.tx * (gp.blx - gm.blx) + T.ty * (gp.bly - gm.bly) + T.tz * (gp.blz - gm.blz) +
+                 T.xy * (gp.gxy - gm.gxy) + T.xz * (gp.gxz - gm.gxz) + T.yz * (gp.gyz - gm.gyz));
+  return s;
+}
+
+// max over active axes of max|lambda| / dx at a cell centre (plus the cleaning speed).
+template <bool YA, bool ZA, bool CLEAN, bool DIAG, typename R>
+__device__ __forceinline__ double cell_max_speed(const KParams& kp, const Geom<R>& G, const R P[9],
+                                                 const Consts<R>& c) {
+  const State<R> S = make_state<DIAG>(G, P, c);
+  const R c2 = cms2_of(S, c);
+  R lm, lp;
+  speeds_of<0, DIAG>(G, S, c2, lm, lp);
+  double v = (double)fmax(fabs(lm), fabs(lp)) * kp.idx;
+  if (CLEAN) {
+    clean_speeds<0, DIAG>(G, c.ch, lm, lp);
+    v = fmax(v, (double)fmax(fabs(lm), fabs(lp)) * kp.idx);
+  }
+  if (YA) {
+    speeds_of<1, DIAG>(G, S, c2, lm, lp);
+    v = fmax(v, (double)fmax(fabs(lm), fabs(lp)) * kp.idy);
+    if (CLEAN) {
+      clean_speeds<1, DIAG>(G, c.ch, lm, lp);
+      v = fmax(v, (double)fmax(fabs(lm), fabs(lp)) * kp.idy);
+    }
+  }
+  if (ZA) {
+    speeds_of<2, DIAG>(G, S, c2, lm, lp);
+    v = fmax(v, (double)fmax(fabs(lm), fabs(lp)) * kp.idz);
+    if (CLEAN) {
+      clean_speeds<2, DIAG>(G, c.ch, lm, lp);
+      v = fmax(v, (double)fmax(fabs(lm), fabs(lp)) * kp.idz);
+    }
+  }
+  return v;
+}
+
+// Block reduction of the CFL maximum, the failure count and the largest iteration count.
+template <int NT>
+__device__ __forceinline__ void block_stats(DevScalars* sc, double vloc, int nfail, int maxit,
+                                            bool want_v) {
+  __shared__ double sv[NT / 32];
+  __shared__ int sf[NT / 32], si[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    vloc = fmax(vloc, __shfl_xor_sync(0xffffffffu, vloc, o));
+    nfail += __shfl_xor_sync(0xffffffffu, nfail, o);
+    maxit = max(maxit, __shfl_xor_sync(0xffffffffu, maxit, o));
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sv[w] = vloc;
+    sf[w] = nfail;
+    si[w] = maxit;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    int nf = 0, mi = 0;
+    for (int q = 0; q < NT / 32; ++q) {
+      v = fmax(v, sv[q]);
+      nf += sf[q];
+      mi = max(mi, si[q]);
+    }
+    if (want_v && v > 0.0) atomicMax(&sc->vmax_bits, (unsigned long long)__double_as_longlong(v));
+    if (nf) atomicAdd(&sc->fails, (unsigned long long)nf);
+    if (mi) atomicMax(&sc->maxit, mi);
+  }
+}
+
+// Recovery with atmosphere / floor handling; rewrites U when the cell is reset.
+template <bool CLEAN, bool DIAG>
+__device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G, double U[9],
+                                       const double Pg[9], const Consts<double>& c, double P[9],
+                                       int& iters) {
+  // atmosphere: a cell whose rest-mass density D / sqrt(gamma) = rho W is below rho_atm is not
+  // recovered but set to the atmosphere state (the decision uses the conserved state only)
+  const bool atm = U[U_D] < kp.rho_atm * G.sqrtg;
+  C2PResult r = {1, 0};
+  if (!atm) r = con2prim<CLEAN, DIAG>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_tol, P);
+  iters = r.iters;
+  bool reset = false;
+  if (atm || !r.ok || P[P_RHO] < kp.rho_floor) {
+    const double isg = 1.0 / G.sqrtmg;
+    P[P_BX] = U[U_BX] * isg;
+    P[P_BY] = U[U_BY] * isg;
+    P[P_BZ] = U[U_BZ] * isg;
+    P[P_PSI] = CLEAN ? U[U_PSI] / G.sqrtg : 0.0;
+    P[P_RHO] = kp.rho_floor;
+    P[P_PRS] = kp.p_atm;
+    P[P_UX] = P[P_UY] = P[P_UZ] = 0.0;
+    reset = true;
+  } else if (P[P_PRS] < kp.p_floor) {
+    P[P_PRS] = kp.p_floor;
+    reset = true;
+  }
+  if (reset) {
+    const State<double> S = make_state<DIAG>(G, P, c);
+    cons_of<CLEAN>(G, S, U);
+  }
+  return r.ok ? 0 : 1;
+}
+
+template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED>
+__global__ void __launch_bounds__(TX * TY, 2)
+k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* __restrict__ M,
+          DevScalars* sc) {
+  using R = typename Prec<MIXED>::R;
+  using S = typename Prec<MIXED>::S;
+  constexpr int NT = TX * TY;
+  constexpr int NV = CLEAN ? 9 : 8;
+  __shared__ R fx[NV][TY][TX + 1];
+  __shared__ R fy[YA ? NV : 1][YA ? TY + 1 : 1][TX];
+  __shared__ R fz[ZA ? 2 : 1][ZA ? NV : 1][TY][TX];
+
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i = i0 + tx, j = j0 + ty;
+  const int kz0 = blockIdx.z * kp.zlen;
+  const int kz1 = min(kz0 + kp.zlen, kp.nz);
+  const bool own = i < kp.nx && j < kp.ny;
+  const double dt = sc->dt;
+  const Consts<R> c = consts_of<R>(kp);
+  const Consts<double> cd = consts_of<double>(kp);
+  const S* __restrict__ P = (const S*)sa.Pin;
+  S* __restrict__ Pout = (S*)sa.Pout;
+
+  double vloc = 0.0;
+  int nfail = 0, maxit = 0;
+
+  if (ZA && own) face_flux<2, CLEAN, DIAG>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX);
+
+  for (int k = kz0; k < kz1; ++k) {
+    // ---- faces of plane k: each face of the tile once
+    if (i <= kp.nx && j < kp.ny) face_flux<0, CLEAN, DIAG>(kp, P, M, i, j, k, &fx[0][ty][tx], TY * (TX + 1));
+    if (YA && i < kp.nx && j <= kp.ny) face_flux<1, CLEAN, DIAG>(kp, P, M, i, j, k, &fy[0][ty][tx], (TY + 1) * TX);
+    if (ZA && own) face_flux<2, CLEAN, DIAG>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
+    if (YA) {
+      // top row of y-faces of the tile: warp 0; right column of x-faces: warp 1
+      if (threadIdx.x < TX) {
+        const int ii = i0 + threadIdx.x, jj = j0 + TY;
+        if (ii < kp.nx && jj <= kp.ny)
+          face_flux<1, CLEAN, DIAG>(kp, P, M, ii, jj, k, &fy[0][TY][threadIdx.x], (TY + 1) * TX);
+      } else if (threadIdx.x >= 32 && threadIdx.x < 32 + TY) {
+        const int jj = j0 + (threadIdx.x - 32), ii = i0 + TX;
+        if (ii <= kp.nx && jj < kp.ny)
+          face_flux<0, CLEAN, DIAG>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x - 32][TX], TY * (TX + 1));
+      }
+    } else if (threadIdx.x < TY) {
+      const int jj = j0 + threadIdx.x, ii = i0 + TX;
+      if (ii <= kp.nx && jj < kp.ny)
+        face_flux<0, CLEAN, DIAG>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x][TX], TY * (TX + 1));
+    }
+    __syncthreads();
+
+    // ---- cell update of plane k
+    if (own) {
+      const long long off = (long long)k * kp.plane + (long long)j * kp.pitch + i;
+      const long long mo = met_off(kp, i, j, k);
+      R L[9];
+#pragma unroll
+      for (int f = 0; f < NV; ++f) {
+        R v = -(fx[f][ty][tx + 1] - fx[f][ty][tx]) * (R)kp.idx;
+        if (YA) v -= (fy[f][ty + 1][tx] - fy[f][ty][tx]) * (R)kp.idy;
+        if (ZA) v -= (fz[(k + 1) & 1][f][ty][tx] - fz[k & 1][f][ty][tx]) * (R)kp.idz;
+        L[f] = v;
+      }
+      // metric source 1/2 sqrt(-g) T^{ab} d_i g_ab (static metric: no energy source)
+      R mc[10];
+      load_metric<DIAG>(kp, M, mo, mc);
+      const Geom<R> G = make_geom<DIAG>(mc);
+      R Pc[9];
+#pragma unroll
+      for (int f = 0; f < NV; ++f) Pc[f] = (R)__ldg(P + f * kp.fs + off);
+      if (!CLEAN) Pc[8] = R(0);
+      {
+        const State<R> St = make_state<DIAG>(G, Pc, c);
+        const Tup<R> T = tup_of<DIAG>(G, St);
+        const R h = R(0.5) * G.sqrtmg;
+        {
+          const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + 1), gm = g4_at<DIAG, R>(kp, M, mo - 1);
+          L[U_TX] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idx);
+        }
+        if (YA) {
+          const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + kp.mpitch), gm = g4_at<DIAG, R>(kp, M, mo - kp.mpitch);
+          L[U_TY] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idy);
+        }
+        if (ZA) {
+          const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + kp.mplane), gm = g4_at<DIAG, R>(kp, M, mo - kp.mplane);
+          L[U_TZ] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idz);
+        }
+        if (CLEAN) L[U_PSI] += -(R)kp.kappa * G.alp * (G.sqrtg * St.psi);
+      }
+      // Runge-Kutta stage (FP64)
+      double U[9];
+#pragma unroll
+      for (int f = 0; f < NV; ++f) {
+        const double uk = sa.Uk[f * kp.fs + off];
+        double u = sa.ak * (uk + dt * (double)L[f]);
+        if (sa.a0 != 0.0) u += sa.a0 * sa.U0[f * kp.fs + off];
+        U[f] = u;
+      }
+      if (!CLEAN) U[8] = 0.0;
+      // recovery of the new primitive state (FP64)
+      double Pg[9], Pn[9];
+#pragma unroll
+      for (int f = 0; f < 9; ++f) Pg[f] = (double)Pc[f];
+      int it;
+      if constexpr (MIXED) {
+        double md[10];
+        load_metric<DIAG>(kp, M, mo, md);
+        const Geom<double> Gd = make_geom<DIAG>(md);
+        nfail += recover<CLEAN, DIAG>(kp, Gd, U, Pg, cd, Pn, it);
+      } else {
+        nfail += recover<CLEAN, DIAG>(kp, G, U, Pg, cd, Pn, it);
+      }
+      maxit = max(maxit, it);
+#pragma unroll
+      for (int f = 0; f < NV; ++f) {
+        sa.Uout[f * kp.fs + off] = U[f];
+        Pout[f * kp.fs + off] = (S)Pn[f];
+      }
+      if (sa.last) {
+        R Pr[9];
+#pragma unroll
+        for (int f = 0; f < 9; ++f) Pr[f] = (R)(S)Pn[f];
+        vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pr, c));
+      }
+    }
+    __syncthreads();
+  }
+  block_stats<NT>(sc, vloc, nfail, maxit, sa.last != 0);
+}
+
+// Conserved state from the primitive state, per cell (FP64 arithmetic on the stored values).
+template <bool CLEAN, bool DIAG, bool MIXED>
+__global__ void k_prim2cons(const KParams kp, const typename Prec<MIXED>::S* __restrict__ P,
+                            const typename Prec<MIXED>::S* __restrict__ M, double* __restrict__ U) {
+  const long long n = (long long)kp.nx * kp.ny * kp.nz;
+  const Consts<double> c = consts_of<double>(kp);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % kp.nx);
+    const int j = (int)((q / kp.nx) % kp.ny);
+    const int k = (int)(q / ((long long)kp.nx * kp.ny));
+    const long long off = (long long)k * kp.plane + (long long)j * kp.pitch + i;
+    double m[10], Pc[9], Uc[9];
+    load_metric<DIAG>(kp, M, met_off(kp, i, j, k), m);
+#pragma unroll
+    for (int f = 0; f < 9; ++f) Pc[f] = (double)P[f * kp.fs + off];
+    if (!CLEAN) Pc[8] = 0.0;
+    const Geom<double> G = make_geom<DIAG>(m);
+    const State<double> S = make_state<DIAG>(G, Pc, c);
+    cons_of<CLEAN>(G, S, Uc);
+    if (!CLEAN) Uc[8] = 0.0;
+#pragma unroll
+    for (int f = 0; f < 9; ++f) U[f * kp.fs + off] = Uc[f];
+  }
+}
+
+template <bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED>
+__global__ void __launch_bounds__(256) k_max_speed(const KParams kp, const typename Prec<MIXED>::S* __restrict__ P,
+                                                   const typename Prec<MIXED>::S* __restrict__ M,
+                                                   DevScalars* sc) {
+  using R = typename Prec<MIXED>::R;
+  const long long n = (long long)kp.nx * kp.ny * kp.nz;
+  const Consts<R> c = consts_of<R>(kp);
+  double v = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % kp.nx);
+    const int j = (int)((q / kp.nx) % kp.ny);
+    const int k = (int)(q / ((long long)kp.nx * kp.ny));
+    const long long off = (long long)k * kp.plane + (long long)j * kp.pitch + i;
+    R m[10], Pc[9];
+    load_metric<DIAG>(kp, M, met_off(kp, i, j, k), m);
+#pragma unroll
+    for (int f = 0; f < 9; ++f) Pc[f] = (R)P[f * kp.fs + off];
+    if (!CLEAN) Pc[8] = R(0);
+    const Geom<R> G = make_geom<DIAG>(m);
+    v = fmax(v, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pc, c));
+  }
+  block_stats<256>(sc, v, 0, 0, true);
+}
+
+inline int grid_blocks(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// Launchers for one (precision, dimensionality); dispatch on cleaning and metric class.
+template <bool YA, bool ZA, bool MIXED>
+void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, const void* Mv,
+                      DevScalars* sc, int zchunks, cudaStream_t st) {
+  constexpr int TX = (!YA && !ZA) ? 128 : 32;
+  constexpr int TY = (!YA && !ZA) ? 1 : 4;
+  using S = typename Prec<MIXED>::S;
+  const S* M = (const S*)Mv;
+  dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, zchunks);
+  if (v.clean) {
+    if (v.diag) k_substep<TX, TY, YA, ZA, true, true, MIXED><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    else k_substep<TX, TY, YA, ZA, true, false, MIXED><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+  } else {
+    if (v.diag) k_substep<TX, TY, YA, ZA, false, true, MIXED><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    else k_substep<TX, TY, YA, ZA, false, false, MIXED><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+  }
+}
+
+template <bool YA, bool ZA, bool MIXED>
+void launch_max_speed_t(const Variant& v, const KParams& kp, const void* Pv, const void* Mv,
+                        DevScalars* sc, cudaStream_t st) {
+  using S = typename Prec<MIXED>::S;
+  const S* P = (const S*)Pv;
+  const S* M = (const S*)Mv;
+  const long long n = (long long)kp.nx * kp.ny * kp.nz;
+  const int nb = grid_blocks(n, 256);
+  if (v.clean) {
+    if (v.diag) k_max_speed<YA, ZA, true, true, MIXED><<<nb, 256, 0, st>>>(kp, P, M, sc);
+    else k_max_speed<YA, ZA, true, false, MIXED><<<nb, 256, 0, st>>>(kp, P, M, sc);
+  } else {
+    if (v.diag) k_max_speed<YA, ZA, false, true, MIXED><<<nb, 256, 0, st>>>(kp, P, M, sc);
+    else k_max_speed<YA, ZA, false, false, MIXED><<<nb, 256, 0, st>>>(kp, P, M, sc);
+  }
+}
+
+template <bool MIXED>
+void launch_prim2cons_t(const Variant& v, const KParams& kp, const void* Pv, const void* Mv,
+                        double* U, cudaStream_t st) {
+  using S = typename Prec<MIXED>::S;
+  const S* P = (const S*)Pv;
+  const S* M = (const S*)Mv;
+  const long long n = (long long)kp.nx * kp.ny * kp.nz;
+  const int nb = grid_blocks(n, 256);
+  if (v.clean) {
+    if (v.diag) k_prim2cons<true, true, MIXED><<<nb, 256, 0, st>>>(kp, P, M, U);
+    else k_prim2cons<true, false, MIXED><<<nb, 256, 0, st>>>(kp, P, M, U);
+  } else {
+    if (v.diag) k_prim2cons<false, true, MIXED><<<nb, 256, 0, st>>>(kp, P, M, U);
+    else k_prim2cons<false, false, MIXED><<<nb, 256, 0, st>>>(kp, P, M, U);
+  }
+}
+
+}  // namespace hzn

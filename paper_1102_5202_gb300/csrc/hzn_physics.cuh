@@ -3,8 +3,12 @@
 // State algebra of §2.1 (u^mu, b^mu, T^mu_nu, the conserved vector and the flux vector of
 // Eq. 2), the fast-magnetosonic speeds used by the HLLE solver (§2.2, §3.2), the MC limiter
 // (§3.2), and the Newton-Raphson recovery of the primitive variables (§2.2, §3.2: the 2D
-// scheme in the unknowns Z = rho h W^2 and v^2).  Everything is written for the real type R
-// so that the same code serves FP64 and the FP32 parts of the mixed-precision path.
+// scheme in the unknowns Z = rho h W^2 and v^2).
+//
+// Everything is written for the real type R (double for the FP64 path; float for the face,
+// flux and source work of the mixed-precision path) and for two metric classes: DIAG (zero
+// shift, diagonal gamma_ij -- Minkowski, isotropic and conformally flat static metrics) and
+// the general 3+1 metric.  DIAG drops terms that are identically zero, nothing else.
 //
 // Variables: primitive u~^i = W v^i = u^i + W beta^i / alpha (§5.2 footnote); B^i = *F^{it};
 // Eulerian field Bn^i = alpha B^i; enthalpy density w = rho + gamma/(gamma-1) p; magnetic
@@ -13,6 +17,7 @@
 
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 namespace hzn {
 
@@ -25,6 +30,7 @@ template <typename R>
 struct Consts {
   R gamma;  // adiabatic index
   R gfac;   // gamma / (gamma - 1)
+  R ch;     // cleaning speed
   R ch2;    // cleaning speed squared
 };
 
@@ -41,37 +47,52 @@ struct Geom {
   R sqrtg, sqrtmg;                  // sqrt(gamma), sqrt(-g) = alpha sqrt(gamma)
 };
 
-template <typename R>
+template <bool DIAG, typename R>
 __device__ __forceinline__ Geom<R> make_geom(const R m[10]) {
   Geom<R> G;
   G.alp = m[M_ALP];
   G.ialp = R(1) / G.alp;
-  G.bx = m[M_BX];
-  G.by = m[M_BY];
-  G.bz = m[M_BZ];
   G.gxx = m[M_GXX];
-  G.gxy = m[M_GXY];
-  G.gxz = m[M_GXZ];
   G.gyy = m[M_GYY];
-  G.gyz = m[M_GYZ];
   G.gzz = m[M_GZZ];
-  const R cxx = G.gyy * G.gzz - G.gyz * G.gyz;
-  const R cxy = G.gxz * G.gyz - G.gxy * G.gzz;
-  const R cxz = G.gxy * G.gyz - G.gyy * G.gxz;
-  const R det = G.gxx * cxx + G.gxy * cxy + G.gxz * cxz;
-  const R idet = R(1) / det;
-  G.ixx = cxx * idet;
-  G.ixy = cxy * idet;
-  G.ixz = cxz * idet;
-  G.iyy = (G.gxx * G.gzz - G.gxz * G.gxz) * idet;
-  G.iyz = (G.gxy * G.gxz - G.gxx * G.gyz) * idet;
-  G.izz = (G.gxx * G.gyy - G.gxy * G.gxy) * idet;
-  G.sqrtg = sqrt(det);
+  if constexpr (DIAG) {
+    G.bx = G.by = G.bz = R(0);
+    G.blx = G.bly = G.blz = R(0);
+    G.gxy = G.gxz = G.gyz = R(0);
+    G.ixy = G.ixz = G.iyz = R(0);
+    const R gyz2 = G.gyy * G.gzz;
+    const R det = G.gxx * gyz2;
+    const R idet = R(1) / det;
+    G.ixx = gyz2 * idet;
+    G.iyy = (G.gxx * G.gzz) * idet;
+    G.izz = (G.gxx * G.gyy) * idet;
+    G.sqrtg = sqrt(det);
+    G.gtt = -G.alp * G.alp;
+  } else {
+    G.bx = m[M_BX];
+    G.by = m[M_BY];
+    G.bz = m[M_BZ];
+    G.gxy = m[M_GXY];
+    G.gxz = m[M_GXZ];
+    G.gyz = m[M_GYZ];
+    const R cxx = G.gyy * G.gzz - G.gyz * G.gyz;
+    const R cxy = G.gxz * G.gyz - G.gxy * G.gzz;
+    const R cxz = G.gxy * G.gyz - G.gyy * G.gxz;
+    const R det = G.gxx * cxx + G.gxy * cxy + G.gxz * cxz;
+    const R idet = R(1) / det;
+    G.ixx = cxx * idet;
+    G.ixy = cxy * idet;
+    G.ixz = cxz * idet;
+    G.iyy = (G.gxx * G.gzz - G.gxz * G.gxz) * idet;
+    G.iyz = (G.gxy * G.gxz - G.gxx * G.gyz) * idet;
+    G.izz = (G.gxx * G.gyy - G.gxy * G.gxy) * idet;
+    G.sqrtg = sqrt(det);
+    G.blx = G.gxx * G.bx + G.gxy * G.by + G.gxz * G.bz;
+    G.bly = G.gxy * G.bx + G.gyy * G.by + G.gyz * G.bz;
+    G.blz = G.gxz * G.bx + G.gyz * G.by + G.gzz * G.bz;
+    G.gtt = -G.alp * G.alp + (G.blx * G.bx + G.bly * G.by + G.blz * G.bz);
+  }
   G.sqrtmg = G.alp * G.sqrtg;
-  G.blx = G.gxx * G.bx + G.gxy * G.by + G.gxz * G.bz;
-  G.bly = G.gxy * G.bx + G.gyy * G.by + G.gyz * G.bz;
-  G.blz = G.gxz * G.bx + G.gyz * G.by + G.gzz * G.bz;
-  G.gtt = -G.alp * G.alp + (G.blx * G.bx + G.bly * G.by + G.blz * G.bz);
   return G;
 }
 
@@ -92,7 +113,7 @@ struct State {
   R Bx, By, Bz;            // B^i
 };
 
-template <typename R>
+template <bool DIAG, typename R>
 __device__ __forceinline__ State<R> make_state(const Geom<R>& G, const R P[9], const Consts<R>& c) {
   State<R> S;
   S.rho = P[P_RHO];
@@ -103,28 +124,48 @@ __device__ __forceinline__ State<R> make_state(const Geom<R>& G, const R P[9], c
   S.By = P[P_BY];
   S.Bz = P[P_BZ];
   // u_i = gamma_ij u~^j (the shift term of u^i drops out of the spatial covariant part)
-  S.lx = G.gxx * vx + G.gxy * vy + G.gxz * vz;
-  S.ly = G.gxy * vx + G.gyy * vy + G.gyz * vz;
-  S.lz = G.gxz * vx + G.gyz * vy + G.gzz * vz;
+  if constexpr (DIAG) {
+    S.lx = G.gxx * vx;
+    S.ly = G.gyy * vy;
+    S.lz = G.gzz * vz;
+  } else {
+    S.lx = G.gxx * vx + G.gxy * vy + G.gxz * vz;
+    S.ly = G.gxy * vx + G.gyy * vy + G.gyz * vz;
+    S.lz = G.gxz * vx + G.gyz * vy + G.gzz * vz;
+  }
   const R q = R(1) + (S.lx * vx + S.ly * vy + S.lz * vz);
   const R rW = rsqrt(q);
   S.W = q * rW;                    // W = sqrt(1 + gamma_ij u~^i u~^j)
   S.ut = S.W * G.ialp;
   S.iut = G.alp * rW;
-  S.ux = vx - S.ut * G.bx;         // u^i = u~^i - W beta^i / alpha
-  S.uy = vy - S.ut * G.by;
-  S.uz = vz - S.ut * G.bz;
-  S.l_t = -G.alp * S.W + (G.bx * S.lx + G.by * S.ly + G.bz * S.lz);
-  // b^t = B^i u_i ; b^i = (B^i + b^t u^i) / u^t
+  // b^t = B^i u_i
   S.bt = S.Bx * S.lx + S.By * S.ly + S.Bz * S.lz;
+  if constexpr (DIAG) {
+    S.ux = vx;                     // u^i = u~^i - W beta^i / alpha, zero shift
+    S.uy = vy;
+    S.uz = vz;
+    S.l_t = -G.alp * S.W;
+  } else {
+    S.ux = vx - S.ut * G.bx;
+    S.uy = vy - S.ut * G.by;
+    S.uz = vz - S.ut * G.bz;
+    S.l_t = -G.alp * S.W + (G.bx * S.lx + G.by * S.ly + G.bz * S.lz);
+  }
+  // b^i = (B^i + b^t u^i) / u^t ; b_mu = g_{mu nu} b^nu
   S.bx = (S.Bx + S.bt * S.ux) * S.iut;
   S.by = (S.By + S.bt * S.uy) * S.iut;
   S.bz = (S.Bz + S.bt * S.uz) * S.iut;
-  // b_mu = g_{mu nu} b^nu
-  S.b_x = G.blx * S.bt + (G.gxx * S.bx + G.gxy * S.by + G.gxz * S.bz);
-  S.b_y = G.bly * S.bt + (G.gxy * S.bx + G.gyy * S.by + G.gyz * S.bz);
-  S.b_z = G.blz * S.bt + (G.gxz * S.bx + G.gyz * S.by + G.gzz * S.bz);
-  S.b_t = G.gtt * S.bt + (G.blx * S.bx + G.bly * S.by + G.blz * S.bz);
+  if constexpr (DIAG) {
+    S.b_x = G.gxx * S.bx;
+    S.b_y = G.gyy * S.by;
+    S.b_z = G.gzz * S.bz;
+    S.b_t = G.gtt * S.bt;
+  } else {
+    S.b_x = G.blx * S.bt + (G.gxx * S.bx + G.gxy * S.by + G.gxz * S.bz);
+    S.b_y = G.bly * S.bt + (G.gxy * S.bx + G.gyy * S.by + G.gyz * S.bz);
+    S.b_z = G.blz * S.bt + (G.gxz * S.bx + G.gyz * S.by + G.gzz * S.bz);
+    S.b_t = G.gtt * S.bt + (G.blx * S.bx + G.bly * S.by + G.blz * S.bz);
+  }
   S.b2 = S.bt * S.b_t + (S.bx * S.b_x + S.by * S.b_y + S.bz * S.b_z);
   S.w = S.rho + c.gfac * S.p;
   return S;
@@ -149,7 +190,7 @@ __device__ __forceinline__ void cons_of(const Geom<R>& G, const State<R>& S, R U
 // Flux vector along D (§2.1 Eq. 2): sqrt(-g) rho u^D, sqrt(-g) T^D_nu, and the induction flux
 // sqrt(-g)(b^j u^D - b^D u^j) = sqrt(-g)(B^j u^D - B^D u^j) / u^t; cleaning adds
 // sqrt(-g) gamma^{Dj} psi to B^j and sqrt(gamma)(c_h^2 alpha^2 B^D - beta^D psi) on Psi.
-template <int D, bool CLEAN, typename R>
+template <int D, bool CLEAN, bool DIAG, typename R>
 __device__ __forceinline__ void flux_of(const Geom<R>& G, const State<R>& S, const Consts<R>& c,
                                         R F[9]) {
   const R wt = S.w + S.b2, pt = S.p + R(0.5) * S.b2;
@@ -168,10 +209,17 @@ __device__ __forceinline__ void flux_of(const Geom<R>& G, const State<R>& S, con
   F[U_BZ] = D == 2 ? R(0) : f * (S.Bz * ud - Bd * S.uz);
   if (CLEAN) {
     const R gp = G.sqrtmg * S.psi;
-    F[U_BX] += gp * sel<D>(G.ixx, G.ixy, G.ixz);
-    F[U_BY] += gp * sel<D>(G.ixy, G.iyy, G.iyz);
-    F[U_BZ] += gp * sel<D>(G.ixz, G.iyz, G.izz);
-    F[U_PSI] = G.sqrtg * (c.ch2 * G.alp * G.alp * Bd - sel<D>(G.bx, G.by, G.bz) * S.psi);
+    if constexpr (DIAG) {
+      if (D == 0) F[U_BX] += gp * G.ixx;
+      if (D == 1) F[U_BY] += gp * G.iyy;
+      if (D == 2) F[U_BZ] += gp * G.izz;
+      F[U_PSI] = G.sqrtg * (c.ch2 * G.alp * G.alp * Bd);
+    } else {
+      F[U_BX] += gp * sel<D>(G.ixx, G.ixy, G.ixz);
+      F[U_BY] += gp * sel<D>(G.ixy, G.iyy, G.iyz);
+      F[U_BZ] += gp * sel<D>(G.ixz, G.iyz, G.izz);
+      F[U_PSI] = G.sqrtg * (c.ch2 * G.alp * G.alp * Bd - sel<D>(G.bx, G.by, G.bz) * S.psi);
+    }
   }
 }
 
@@ -186,18 +234,23 @@ __device__ __forceinline__ R cms2_of(const State<R>& S, const Consts<R>& c) {
 
 // Characteristic speeds along D: roots of A l^2 + B l + C = 0 from the dispersion relation
 // (u^D - l u^t)^2 = c^2 [g^tt l^2 - 2 g^tD l + g^DD + (u^D - l u^t)^2].
-template <int D, typename R>
+template <int D, bool DIAG, typename R>
 __device__ __forceinline__ void speeds_of(const Geom<R>& G, const State<R>& S, R c2, R& lm, R& lp) {
   const R ia2 = G.ialp * G.ialp;
-  const R bd = sel<D>(G.bx, G.by, G.bz);
-  const R gtt = -ia2;
-  const R gtd = bd * ia2;
-  const R gdd = sel<D>(G.ixx, G.iyy, G.izz) - bd * bd * ia2;
   const R ud = sel<D>(S.ux, S.uy, S.uz);
   const R oc = R(1) - c2;
-  const R A = oc * S.ut * S.ut - c2 * gtt;
-  const R B = R(-2) * (oc * S.ut * ud - c2 * gtd);
-  const R C = oc * ud * ud - c2 * gdd;
+  const R A = oc * S.ut * S.ut + c2 * ia2;  // - c^2 g^tt, g^tt = -1/alpha^2
+  R B, C;
+  if constexpr (DIAG) {
+    B = R(-2) * (oc * S.ut * ud);
+    C = oc * ud * ud - c2 * sel<D>(G.ixx, G.iyy, G.izz);
+  } else {
+    const R bd = sel<D>(G.bx, G.by, G.bz);
+    const R gtd = bd * ia2;
+    const R gdd = sel<D>(G.ixx, G.iyy, G.izz) - bd * bd * ia2;
+    B = R(-2) * (oc * S.ut * ud - c2 * gtd);
+    C = oc * ud * ud - c2 * gdd;
+  }
   R disc = B * B - R(4) * A * C;
   disc = disc > R(0) ? disc : R(0);
   const R sq = sqrt(disc);
@@ -206,185 +259,259 @@ __device__ __forceinline__ void speeds_of(const Geom<R>& G, const State<R>& S, R
   lm = (-B - sq) * i2a;
 }
 
-// Coordinate speed bound of the cleaning pair along D: |beta^D| + c_h alpha sqrt(gamma^DD).
-template <int D, typename R>
+// Coordinate speeds of the cleaning pair along D: -beta^D -+ c_h alpha sqrt(gamma^DD).
+template <int D, bool DIAG, typename R>
 __device__ __forceinline__ void clean_speeds(const Geom<R>& G, R ch, R& lm, R& lp) {
   const R a = ch * G.alp * sqrt(sel<D>(G.ixx, G.iyy, G.izz));
-  const R bd = sel<D>(G.bx, G.by, G.bz);
-  lm = -bd - a;
-  lp = -bd + a;
+  if constexpr (DIAG) {
+    lm = -a;
+    lp = a;
+  } else {
+    const R bd = sel<D>(G.bx, G.by, G.bz);
+    lm = -bd - a;
+    lp = -bd + a;
+  }
 }
 
-// Monotonized-central limited slope (TVD reconstruction with the MC limiter, §3.2).
-template <typename R>
-__device__ __forceinline__ R mc_slope(R dm, R dp) {
-  const R a = fmin(fmin(R(2) * fabs(dm), R(2) * fabs(dp)), R(0.5) * fabs(dm + dp));
-  const R s = dp > R(0) ? a : -a;
-  return dm * dp > R(0) ? s : R(0);
+// Half of the monotonized-central limited slope (TVD reconstruction with the MC limiter,
+// §3.2): sign(dp) min(|dm|, |dp|, |dm + dp| / 4) when dm and dp have the same strict sign,
+// else 0.  The face values are P_i -+ this.  For FP64 the sign test and the three-way minimum
+// are taken on the IEEE bit patterns (the order of non-negative doubles is the order of their
+// bits), so that only the sum and the exact quarter run on the FP64 pipe; the result is the
+// same number the floating-point comparisons give.
+__device__ __forceinline__ double mc_half_slope(double dm, double dp) {
+  const long long bm = __double_as_longlong(dm), bp = __double_as_longlong(dp);
+  const long long am = bm & 0x7fffffffffffffffLL, ap = bp & 0x7fffffffffffffffLL;
+  const long long aq = __double_as_longlong(0.25 * (dm + dp)) & 0x7fffffffffffffffLL;
+  long long m = am < ap ? am : ap;
+  m = m < aq ? m : aq;
+  const bool same = ((bm ^ bp) >= 0) && am != 0 && ap != 0;
+  const long long r = same ? (m | (bp & (long long)0x8000000000000000ULL)) : 0LL;
+  return __longlong_as_double(r);
+}
+
+__device__ __forceinline__ float mc_half_slope(float dm, float dp) {
+  const float a = fminf(fminf(fabsf(dm), fabsf(dp)), 0.25f * fabsf(dm + dp));
+  const float s = dp > 0.f ? a : -a;
+  return dm * dp > 0.f ? s : 0.f;
 }
 
 // ------------------------------------------------------------------------------------------
 // Recovery of the primitive state from the conserved one (§2.2: Newton-Raphson, §3.2: the 2D
-// scheme).  With normal-observer quantities D = rho W, S_i, E, Bn^i and the unknowns
-// Z = w W^2, v^2 the conserved data satisfy
-//   r1 = (Z + Bn^2)^2 v^2 - (S.Bn)^2 (2Z + Bn^2) / Z^2 - S^2 = 0
-//   r2 = Z - p + Bn^2 (1 + v^2)/2 - (S.Bn)^2 / (2 Z^2) - E = 0,
-//   p  = (gamma - 1)/gamma (Z (1 - v^2) - D sqrt(1 - v^2)),
-// solved by Newton with the analytic 2x2 Jacobian from the previous primitive state.
+// scheme).  With normal-observer quantities D = rho W, S_i, E, Bn^i, and the unknowns
+// z = Z / D = w W^2 / D and v^2 (scaled by D so that every quantity is O(1), which keeps the
+// FP32 stage of the iteration in range for any density), the conserved data satisfy
+//   r1 = (z + b)^2 v^2 - q (2z + b) / z^2 - s = 0
+//   r2 = z - p + b (1 + v^2)/2 - q / (2 z^2) - e = 0,
+//   p  = (gamma - 1)/gamma (z (1 - v^2) - sqrt(1 - v^2)),
+// with b = Bn^2 / D, s = S^2 / D^2, q = (S.Bn)^2 / D^3, e = E / D and p the pressure over D.
+// Newton with the analytic 2x2 Jacobian runs in FP32 from the previous primitive state until
+// it settles to FP32 accuracy, then in FP64 to the tolerance; a bracketed 1D solve takes over
+// if the FP64 iteration does not settle.
 // ------------------------------------------------------------------------------------------
 struct C2PResult {
   int ok;
   int iters;
 };
 
-// Normal-observer invariants of one conserved state: D, E, S^2, (S.Bn)^2, Bn^2, (gamma-1)/gamma.
+// Scaled invariants of one conserved state.
 struct C2PScalars {
-  double D, E, S2, SB2, B2, g1;
+  double e, s, q, b, g1;
 };
 
-__device__ __forceinline__ double c2p_v2(const C2PScalars& q, double Z) {
-  const double ZB = Z + q.B2;
-  return (Z * Z * q.S2 + q.SB2 * (2.0 * Z + q.B2)) / (Z * Z * ZB * ZB);
+template <typename R>
+struct NewtonStep {
+  R dz, dv;
+};
+
+template <typename R>
+__device__ __forceinline__ NewtonStep<R> c2p_newton(R z, R v2, R e, R s, R q, R b, R g1) {
+  const R sq = sqrt(R(1) - v2);
+  const R iz = R(1) / z;
+  const R iz2 = iz * iz;
+  const R zb = z + b;
+  const R p = g1 * (z * (R(1) - v2) - sq);
+  const R r1 = zb * zb * v2 - q * (R(2) * z + b) * iz2 - s;
+  const R r2 = z - p + R(0.5) * b * (R(1) + v2) - R(0.5) * q * iz2 - e;
+  const R j11 = R(2) * zb * v2 + R(2) * q * zb * iz2 * iz;
+  const R j12 = zb * zb;
+  const R j21 = R(1) - g1 * (R(1) - v2) + q * iz2 * iz;
+  const R j22 = g1 * (z - R(0.5) / sq) + R(0.5) * b;
+  const R idet = R(1) / (j11 * j22 - j12 * j21);
+  NewtonStep<R> st;
+  st.dz = -(j22 * r1 - j12 * r2) * idet;
+  st.dv = -(j11 * r2 - j21 * r1) * idet;
+  return st;
 }
 
-// Energy residual with v^2 = v^2(Z) substituted, and its Z derivative.
-__device__ __forceinline__ double c2p_f1d(const C2PScalars& q, double Z, double* dfdZ) {
-  const double ZB = Z + q.B2;
-  const double N = Z * Z * q.S2 + q.SB2 * (2.0 * Z + q.B2);
-  const double Dn = Z * Z * ZB * ZB;
+__device__ __forceinline__ double c2p_v2(const C2PScalars& q, double z) {
+  const double zb = z + q.b;
+  return (z * z * q.s + q.q * (2.0 * z + q.b)) / (z * z * zb * zb);
+}
+
+// Energy residual with v^2 = v^2(z) substituted, and its z derivative.
+__device__ __forceinline__ double c2p_f1d(const C2PScalars& q, double z, double* dfdz) {
+  const double zb = z + q.b;
+  const double N = z * z * q.s + q.q * (2.0 * z + q.b);
+  const double Dn = z * z * zb * zb;
   const double v2 = N / Dn;
-  const double dv2 = ((2.0 * Z * q.S2 + 2.0 * q.SB2) * Dn - N * (2.0 * Z * ZB * (2.0 * Z + q.B2))) / (Dn * Dn);
+  const double dv2 = ((2.0 * z * q.s + 2.0 * q.q) * Dn - N * (2.0 * z * zb * (2.0 * z + q.b))) / (Dn * Dn);
   const double sq = sqrt(1.0 - v2);
-  const double p = q.g1 * (Z * (1.0 - v2) - q.D * sq);
-  const double iZ2 = 1.0 / (Z * Z);
-  *dfdZ = 1.0 - q.g1 * (1.0 - v2) - q.g1 * (0.5 * q.D / sq - Z) * dv2 + 0.5 * q.B2 * dv2 +
-          q.SB2 * iZ2 / Z;
-  return Z - p + 0.5 * q.B2 * (1.0 + v2) - 0.5 * q.SB2 * iZ2 - q.E;
+  const double p = q.g1 * (z * (1.0 - v2) - sq);
+  const double iz2 = 1.0 / (z * z);
+  *dfdz = 1.0 - q.g1 * (1.0 - v2) - q.g1 * (0.5 / sq - z) * dv2 + 0.5 * q.b * dv2 + q.q * iz2 / z;
+  return z - p + 0.5 * q.b * (1.0 + v2) - 0.5 * q.q * iz2 - q.e;
 }
 
-// Fallback recovery: Newton on the 1D residual kept inside a bracket [Zlo, gamma E] by
-// bisection (the 'rtsafe' safeguard of Press et al.).  gamma E bounds Z from above because
-// E >= Z - p >= Z / gamma; Zlo is found by bisection where v^2(Z) drops below 1 - 1e-12.
+// Fallback recovery: Newton on the 1D residual kept inside a bracket [zlo, gamma e] by
+// bisection (the 'rtsafe' safeguard of Press et al.).  gamma e bounds z from above because
+// E >= Z - p >= Z / gamma; zlo is found by bisection where v^2(z) drops below 1 - 1e-12.
 // Returns false when no root is bracketed (an unphysical conserved state).
-__device__ __noinline__ bool c2p_bracketed(const C2PScalars q, double Zguess, double& Zout,
+static __device__ __noinline__ bool c2p_bracketed(const C2PScalars q, double zguess, double& zout,
                                            double& v2out, int& iters) {
   const double v2cap = 1.0 - 1e-12;
-  const double Zhi = q.E / (1.0 - q.g1);  // gamma E
-  if (!(c2p_v2(q, Zhi) < v2cap)) return false;
-  double Zlo = Zhi * 1e-100;
-  if (!(c2p_v2(q, Zlo) < v2cap)) {
-    double a = Zlo, b = Zhi;
+  const double zhi = q.e / (1.0 - q.g1);  // gamma e
+  if (!(c2p_v2(q, zhi) < v2cap)) return false;
+  double zlo = zhi * 1e-100;
+  if (!(c2p_v2(q, zlo) < v2cap)) {
+    double a = zlo, b = zhi;
     for (int k = 0; k < 400 && b - a > 1e-14 * b; ++k) {
       const double m = 0.5 * (a + b);
       if (c2p_v2(q, m) < v2cap) b = m; else a = m;
     }
-    Zlo = b;
+    zlo = b;
   }
   double df;
-  if (!(c2p_f1d(q, Zlo, &df) < 0.0)) return false;
-  if (!(c2p_f1d(q, Zhi, &df) >= 0.0)) return false;
-  double lo = Zlo, hi = Zhi;
-  double Z = (Zguess > lo && Zguess < hi) ? Zguess : 0.5 * (lo + hi);
+  if (!(c2p_f1d(q, zlo, &df) < 0.0)) return false;
+  if (!(c2p_f1d(q, zhi, &df) >= 0.0)) return false;
+  double lo = zlo, hi = zhi;
+  double z = (zguess > lo && zguess < hi) ? zguess : 0.5 * (lo + hi);
   for (int it = 0; it < 200; ++it) {
     ++iters;
-    const double f = c2p_f1d(q, Z, &df);
+    const double f = c2p_f1d(q, z, &df);
     if (f == 0.0) break;
-    if (f < 0.0) lo = Z; else hi = Z;
-    double Zn = Z - f / df;
-    if (!(Zn > lo && Zn < hi)) Zn = 0.5 * (lo + hi);
-    const bool conv = fabs(Zn - Z) <= 1e-15 * Z || hi - lo <= 4e-16 * hi;
-    Z = Zn;
+    if (f < 0.0) lo = z; else hi = z;
+    double zn = z - f / df;
+    if (!(zn > lo && zn < hi)) zn = 0.5 * (lo + hi);
+    const bool conv = fabs(zn - z) <= 1e-15 * z || hi - lo <= 4e-16 * hi;
+    z = zn;
     if (conv) break;
   }
-  const double v2 = c2p_v2(q, Z);
-  if (!(v2 < 1.0) || !(Z > 0.0)) return false;
-  Zout = Z;
+  const double v2 = c2p_v2(q, z);
+  if (!(v2 < 1.0) || !(z > 0.0)) return false;
+  zout = z;
   v2out = v2;
   return true;
 }
 
-template <bool CLEAN>
+// Guarded Newton update: keep z > 0 and 0 <= v^2 < 1.
+template <typename R>
+__device__ __forceinline__ void c2p_apply(R& z, R& v2, NewtonStep<R> st) {
+  R zn = z + st.dz;
+  R vn = v2 + st.dv;
+  if (!(zn > R(0))) zn = R(0.5) * z;
+  if (vn < R(0)) vn = R(0);
+  if (!(vn < R(1))) vn = R(0.5) * (v2 + R(1));
+  z = zn;
+  v2 = vn;
+}
+
+// Recovery at one cell.  G is the FP64 centre geometry; U the FP64 conserved vector; Pg the
+// previous primitive state (initial guess).  maxit caps the FP64 iterations.
+template <bool CLEAN, bool DIAG>
 __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const double U[9],
                                               const double Pg[9], const Consts<double>& c,
                                               int maxit, double tol, double P[9]) {
   const double isg = 1.0 / G.sqrtg;
-  const double D = U[U_D] * isg;
+  const double Dd = U[U_D] * isg;
   const double Sx = U[U_TX] * isg, Sy = U[U_TY] * isg, Sz = U[U_TZ] * isg;
   const double Bx = U[U_BX] * isg, By = U[U_BY] * isg, Bz = U[U_BZ] * isg;
-  const double E = (-U[U_TT] + (G.bx * U[U_TX] + G.by * U[U_TY] + G.bz * U[U_TZ])) * isg * G.ialp;
-  // S^i = gamma^ij S_j ; Bn_i = gamma_ij Bn^j
-  const double Sux = G.ixx * Sx + G.ixy * Sy + G.ixz * Sz;
-  const double Suy = G.ixy * Sx + G.iyy * Sy + G.iyz * Sz;
-  const double Suz = G.ixz * Sx + G.iyz * Sy + G.izz * Sz;
+  double E;
+  double Sux, Suy, Suz, Blx, Bly, Blz;
+  if constexpr (DIAG) {
+    E = -U[U_TT] * isg * G.ialp;
+    Sux = G.ixx * Sx;
+    Suy = G.iyy * Sy;
+    Suz = G.izz * Sz;
+    Blx = G.gxx * Bx;
+    Bly = G.gyy * By;
+    Blz = G.gzz * Bz;
+  } else {
+    E = (-U[U_TT] + (G.bx * U[U_TX] + G.by * U[U_TY] + G.bz * U[U_TZ])) * isg * G.ialp;
+    Sux = G.ixx * Sx + G.ixy * Sy + G.ixz * Sz;
+    Suy = G.ixy * Sx + G.iyy * Sy + G.iyz * Sz;
+    Suz = G.ixz * Sx + G.iyz * Sy + G.izz * Sz;
+    Blx = G.gxx * Bx + G.gxy * By + G.gxz * Bz;
+    Bly = G.gxy * Bx + G.gyy * By + G.gyz * Bz;
+    Blz = G.gxz * Bx + G.gyz * By + G.gzz * Bz;
+  }
   const double S2 = Sux * Sx + Suy * Sy + Suz * Sz;
-  const double Blx = G.gxx * Bx + G.gxy * By + G.gxz * Bz;
-  const double Bly = G.gxy * Bx + G.gyy * By + G.gyz * Bz;
-  const double Blz = G.gxz * Bx + G.gyz * By + G.gzz * Bz;
   const double B2 = Blx * Bx + Bly * By + Blz * Bz;
   const double SB = Sx * Bx + Sy * By + Sz * Bz;
-  const double SB2 = SB * SB;
   const double g1 = (c.gamma - 1.0) / c.gamma;
 
   C2PResult res;
   res.ok = 0;
   res.iters = 0;
-  if (!(D > 0.0) || !(E > 0.0)) return res;
+  if (!(Dd > 0.0) || !(E > 0.0)) return res;
+  const double iD = 1.0 / Dd;
+  C2PScalars q;
+  q.e = E * iD;
+  q.b = B2 * iD;
+  q.s = S2 * iD * iD;
+  q.q = SB * SB * iD * iD * iD;
+  q.g1 = g1;
 
-  // initial guess from the previous primitive state
-  double Z, v2;
+  // initial guess from the previous primitive state: z = w W^2 / D, v^2 = uu / (1 + uu)
+  double z, v2;
   {
     const double vx = Pg[P_UX], vy = Pg[P_UY], vz = Pg[P_UZ];
-    const double uu = (G.gxx * vx + G.gxy * vy + G.gxz * vz) * vx +
-                      (G.gxy * vx + G.gyy * vy + G.gyz * vz) * vy +
-                      (G.gxz * vx + G.gyz * vy + G.gzz * vz) * vz;
+    double uu;
+    if constexpr (DIAG) uu = G.gxx * vx * vx + G.gyy * vy * vy + G.gzz * vz * vz;
+    else
+      uu = (G.gxx * vx + G.gxy * vy + G.gxz * vz) * vx + (G.gxy * vx + G.gyy * vy + G.gyz * vz) * vy +
+           (G.gxz * vx + G.gyz * vy + G.gzz * vz) * vz;
     const double wg = Pg[P_RHO] + c.gfac * Pg[P_PRS];
-    Z = wg * (1.0 + uu);
+    z = wg * (1.0 + uu) * iD;
     v2 = uu / (1.0 + uu);
-    if (!(Z > 0.0)) Z = E;
+    if (!(z > 0.0) || !(z < 1e30)) z = q.e;
   }
+  // FP32 stage
+  {
+    float zf = (float)z, vf = (float)v2;
+    const float ef = (float)q.e, sf = (float)q.s, qf = (float)q.q, bf = (float)q.b, gf = (float)g1;
+    for (int it = 0; it < 30; ++it) {
+      const NewtonStep<float> st = c2p_newton<float>(zf, vf, ef, sf, qf, bf, gf);
+      c2p_apply(zf, vf, st);
+      ++res.iters;
+      if (fabsf(st.dz) <= 3e-6f * zf && fabsf(st.dv) <= 3e-6f) break;
+    }
+    if (zf > 0.f && vf >= 0.f && vf < 1.f && isfinite(zf)) {
+      z = (double)zf;
+      v2 = (double)vf;
+    }
+  }
+  // FP64 stage
   bool done = false;
-  int it = 0;
-  for (; it < maxit; ++it) {
-    const double sq = sqrt(1.0 - v2);
-    const double iZ = 1.0 / Z;
-    const double iZ2 = iZ * iZ;
-    const double ZB = Z + B2;
-    const double p = g1 * (Z * (1.0 - v2) - D * sq);
-    const double r1 = ZB * ZB * v2 - SB2 * (2.0 * Z + B2) * iZ2 - S2;
-    const double r2 = Z - p + 0.5 * B2 * (1.0 + v2) - 0.5 * SB2 * iZ2 - E;
-    const double j11 = 2.0 * ZB * v2 + 2.0 * SB2 * ZB * iZ2 * iZ;
-    const double j12 = ZB * ZB;
-    const double j21 = 1.0 - g1 * (1.0 - v2) + SB2 * iZ2 * iZ;
-    const double j22 = g1 * (Z - 0.5 * D / sq) + 0.5 * B2;
-    const double idet = 1.0 / (j11 * j22 - j12 * j21);
-    const double dZ = -(j22 * r1 - j12 * r2) * idet;
-    const double dv = -(j11 * r2 - j21 * r1) * idet;
-    double Zn = Z + dZ;
-    double vn = v2 + dv;
-    if (!(Zn > 0.0)) Zn = 0.5 * Z;
-    if (vn < 0.0) vn = 0.0;
-    if (!(vn < 1.0)) vn = 0.5 * (v2 + 1.0);
-    const bool conv = fabs(dZ) <= tol * Z && fabs(dv) <= tol;
-    Z = Zn;
-    v2 = vn;
-    if (conv) {
+  for (int it = 0; it < maxit; ++it) {
+    const NewtonStep<double> st = c2p_newton<double>(z, v2, q.e, q.s, q.q, q.b, g1);
+    c2p_apply(z, v2, st);
+    ++res.iters;
+    if (fabs(st.dz) <= tol * z && fabs(st.dv) <= tol) {
       done = true;
-      ++it;
       break;
     }
   }
-  res.iters = it;
-  if (!done || !(v2 < 1.0) || !(Z > 0.0)) {
-    // the 2D iteration did not settle: bracketed 1D solve in Z (v^2 eliminated)
-    const C2PScalars q = {D, E, S2, SB2, B2, g1};
-    if (!c2p_bracketed(q, Z, Z, v2, res.iters)) return res;
+  if (!done || !(v2 < 1.0) || !(z > 0.0)) {
+    if (!c2p_bracketed(q, z, z, v2, res.iters)) return res;
   }
   const double rW = sqrt(1.0 - v2);  // 1/W
   const double W = 1.0 / rW;
-  const double p = g1 * (Z * (1.0 - v2) - D * rW);
+  const double Z = z * Dd;
+  const double p = g1 * (Z * (1.0 - v2) - Dd * rW);
   const double iZB = 1.0 / (Z + B2);
   const double sbz = SB / Z;
-  P[P_RHO] = D * rW;
+  P[P_RHO] = Dd * rW;
   P[P_PRS] = p;
   P[P_UX] = W * (Sux + sbz * Bx) * iZB;
   P[P_UY] = W * (Suy + sbz * By) * iZB;
