@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-tubes", type=int, default=512)
     ap.add_argument("--n-mixed", type=int, default=384, help="cells per axis of the mixed line")
     return ap.parse_args()
 
@@ -226,6 +228,10 @@ def run_gpu(args, rank, world, local):
         torch.cuda.empty_cache()
         mixed = run_mixed(args, dist, local, hbm_peak)
 
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = run_ensemble(args, dist, local)
+
     line = None
     if rank == 0:
         cpu = None
@@ -244,6 +250,7 @@ def run_gpu(args, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "mixed": mixed,
+            "ensemble": ensemble,
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "c2p_failures": int(st.c2p_failures),
@@ -303,6 +310,44 @@ def run_mixed(args, dist, local, hbm_peak):
 
 def world_size(dist):
     return 1 if dist is None else dist.get_world_size()
+
+
+def run_ensemble(args, dist, local):
+    """The batched configuration: 512 independent magnetised tubes (cells U{200..4000}, seed
+    1103) advanced to t = 0.4 at CFL 0.5 in one persistent, graph-captured launch whose block
+    shape the library's autotuner picks.  Zone updates = sum over tubes of cells x steps."""
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+    from paper_1102_5202_gb300 import workloads as W
+
+    tubes = W.ensemble(args.ensemble_tubes, seed=1103)
+    E = hzn.Ensemble(tubes)
+    threads, ctas, probe_ms = E.autotune(t_probe=0.02)
+    E.set_primitives()
+    E.run(0.4, 0.5, use_graph=True)  # warm-up: captures and runs the graph
+    E.stream.synchronize()
+    E.set_primitives()
+    E.stream.synchronize()
+    if dist is not None:
+        dist.barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(E.stream)
+    E.run(0.4, 0.5, use_graph=True)
+    b.record(E.stream)
+    b.synchronize()
+    sec = a.elapsed_time(b) * 1e-3
+    t, steps, fails = E.results()
+    zu = float((E.n.astype(np.float64) * steps).sum())
+    units, seconds = aggregate(zu, sec, dist, device=torch.device("cuda", local))
+    E.close()
+    return {"value": units / seconds, "unit": UNIT, "workload": f"ensemble_{len(tubes)}_tubes_fp64",
+            "tubes": len(tubes), "cells": int(E.n.sum()), "zone_updates": zu, "seconds": seconds,
+            "t_reached_min": float(t.min()), "steps_min": int(steps.min()), "steps_max": int(steps.max()),
+            "c2p_failures": int(fails.sum()), "launch": {"threads": threads, "ctas_per_sm": ctas,
+                                                         "autotune_probe_ms": [round(m, 3) for m in probe_ms]},
+            "graph": True, "gpu_launches": 1}
 
 
 def run_e2e(s, P, args, dist, local):

@@ -142,6 +142,59 @@ const char* hz_strerror(int code);
 /* HZN_VERSION of the loaded library. */
 int hz_version(void);
 
+/* ---- Ensembles of independent 1-D tubes ------------------------------------------------
+ * Many independent 1-D Riemann problems (the shock tubes of §5.1) advanced to a common end
+ * time in one persistent launch.  Each tube has its own cell count n[t] >= 2, cell width dx[t]
+ * and adiabatic index gamma[t], Minkowski spacetime, outflow boundaries, and its own CFL time
+ * step; the scheme is that of the grid path (MC, HLLE, RK3, Newton recovery; §2.2, §3.2) in
+ * FP64 without divergence cleaning (opts->precision = HZ_FP64, opts->cleaning = 0; the floors,
+ * rho_atm, atm_K and the recovery options of hz_options apply).  A persistent grid of thread
+ * blocks takes tubes from a work queue, most cells first; one block owns a tube for all its
+ * steps, so no grid-wide synchronisation is needed.
+ *
+ * Caller layout of primitives: the tubes concatenated without padding and field-major over
+ * the concatenation: field f of cell c of tube t at [f * Ncat + off[t] + c] with
+ * off[t] = n[0] + ... + n[t-1], Ncat = sum n[t]; fields as for the grid (the ninth, psi, is
+ * ignored), 9 x Ncat doubles. */
+typedef struct hz_ensemble hz_ensemble;
+
+/* Device bytes hz_ensemble_create needs for these tube sizes. */
+int hz_ensemble_workspace_bytes(int ntubes, const int* h_n, size_t* bytes);
+
+/* Create an ensemble over caller-owned device workspace (256-byte aligned).  Host arrays of
+ * length ntubes.  Synchronises the device (uploads its tables).  Errors: HZ_ERR_ARG,
+ * HZ_ERR_WORKSPACE, HZ_ERR_UNSUPPORTED (mixed precision or cleaning), HZ_ERR_CUDA. */
+int hz_ensemble_create(hz_ensemble** ens, int ntubes, const int* h_n, const double* h_dx,
+                       const double* h_gamma, const hz_options* opts, void* d_workspace,
+                       size_t bytes, void* stream);
+int hz_ensemble_destroy(hz_ensemble* ens);
+
+/* Copy in the primitive state of every tube (layout above) and compute the conserved state. */
+int hz_ensemble_set_primitives(hz_ensemble* ens, const double* d_prim);
+
+/* Launch shape: threads per block and blocks per SM, one of (64,4), (128,1), (128,2),
+ * (128,3), (256,1).  Default (128,2). */
+int hz_ensemble_set_launch(hz_ensemble* ens, int threads, int ctas_per_sm);
+
+/* Advance every tube from t = 0 to t_end with dt = cfl / max|lambda|/dx of that tube, at most
+ * max_steps steps per tube, in one kernel launch.  use_graph = 1 captures the launch (with
+ * its queue reset) in a CUDA graph on first use and replays the graph afterwards; capture
+ * needs a stream other than the legacy default stream.  Asynchronous. */
+int hz_ensemble_run(hz_ensemble* ens, double t_end, double cfl, long long max_steps, int use_graph);
+
+/* Copy out the primitive state of every tube (layout above). */
+int hz_ensemble_get_primitives(hz_ensemble* ens, double* d_prim);
+
+/* Per-tube time reached, steps taken and recovery failures of the last run (host arrays of
+ * length ntubes).  Synchronises the stream; HZ_WARN_C2P if any tube had failures. */
+int hz_ensemble_results(hz_ensemble* ens, double* h_t, long long* h_steps, long long* h_fails);
+
+/* Autotuner: time a probe run to t_probe for each launch shape above, keep the fastest, and
+ * restore the state from d_prim.  Outputs the chosen shape and, if h_ms is not null, the five
+ * probe times in ms.  Synchronises the stream. */
+int hz_ensemble_autotune(hz_ensemble* ens, const double* d_prim, double t_probe, double cfl,
+                         int* h_threads, int* h_ctas_per_sm, float* h_ms);
+
 /* ---- Whole update without allocation --------------------------------------------------
  * The paper has no counterpart to this call; it is a convenience of this library.
  *

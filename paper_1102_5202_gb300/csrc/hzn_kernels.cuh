@@ -301,7 +301,7 @@ __device__ __forceinline__ void block_stats(DevScalars* sc, double vloc, int nfa
 }
 
 // Recovery with atmosphere / floor handling; rewrites U when the cell is reset.
-template <bool CLEAN, bool DIAG>
+template <bool CLEAN, bool DIAG, bool ONE_FINISH = false>
 __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G, double U[9],
                                        const double Pg[9], const Consts<double>& c, double P[9],
                                        int& iters) {
@@ -309,7 +309,7 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
   // recovered but set to the atmosphere state (the decision uses the conserved state only)
   const bool atm = U[U_D] < kp.rho_atm * G.sqrtg;
   C2PResult r = {1, 0};
-  if (!atm) r = con2prim<CLEAN, DIAG>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_tol, P);
+  if (!atm) r = con2prim<CLEAN, DIAG, ONE_FINISH>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_tol, P);
   iters = r.iters;
   bool reset = false;
   if (atm || !r.ok || P[P_RHO] < kp.rho_floor) {
@@ -334,7 +334,7 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
 }
 
 template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED>
-__global__ void __launch_bounds__(TX * TY, 2)
+__global__ void __launch_bounds__(TX * TY, MIXED ? 3 : 2)
 k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* __restrict__ M,
           DevScalars* sc) {
   using R = typename Prec<MIXED>::R;
@@ -442,7 +442,7 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         double md[10];
         load_metric<DIAG>(kp, M, mo, md);
         const Geom<double> Gd = make_geom<DIAG>(md);
-        nfail += recover<CLEAN, DIAG>(kp, Gd, U, Pg, cd, Pn, it);
+        nfail += recover<CLEAN, DIAG, true>(kp, Gd, U, Pg, cd, Pn, it);
       } else {
         nfail += recover<CLEAN, DIAG>(kp, G, U, Pg, cd, Pn, it);
       }

@@ -417,8 +417,10 @@ __device__ __forceinline__ void c2p_apply(R& z, R& v2, NewtonStep<R> st) {
 }
 
 // Recovery at one cell.  G is the FP64 centre geometry; U the FP64 conserved vector; Pg the
-// previous primitive state (initial guess).  maxit caps the FP64 iterations.
-template <bool CLEAN, bool DIAG>
+// previous primitive state (initial guess).  maxit caps the FP64 iterations.  ONE_FINISH:
+// when the FP32 stage has settled, apply a single FP64 Newton correction (quadratic
+// convergence takes the 1e-7 FP32 error to ~1e-14, ample when the result is stored in FP32).
+template <bool CLEAN, bool DIAG, bool ONE_FINISH = false>
 __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const double U[9],
                                               const double Pg[9], const Consts<double>& c,
                                               int maxit, double tol, double P[9]) {
@@ -477,6 +479,7 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
     if (!(z > 0.0) || !(z < 1e30)) z = q.e;
   }
   // FP32 stage
+  bool settled = false;
   {
     float zf = (float)z, vf = (float)v2;
     const float ef = (float)q.e, sf = (float)q.s, qf = (float)q.q, bf = (float)q.b, gf = (float)g1;
@@ -484,16 +487,27 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
       const NewtonStep<float> st = c2p_newton<float>(zf, vf, ef, sf, qf, bf, gf);
       c2p_apply(zf, vf, st);
       ++res.iters;
-      if (fabsf(st.dz) <= 3e-6f * zf && fabsf(st.dv) <= 3e-6f) break;
+      if (fabsf(st.dz) <= 3e-6f * zf && fabsf(st.dv) <= 3e-6f) {
+        settled = true;
+        break;
+      }
     }
     if (zf > 0.f && vf >= 0.f && vf < 1.f && isfinite(zf)) {
       z = (double)zf;
       v2 = (double)vf;
+    } else {
+      settled = false;
     }
   }
   // FP64 stage
   bool done = false;
-  for (int it = 0; it < maxit; ++it) {
+  if (ONE_FINISH && settled) {
+    const NewtonStep<double> st = c2p_newton<double>(z, v2, q.e, q.s, q.q, q.b, g1);
+    c2p_apply(z, v2, st);
+    ++res.iters;
+    done = fabs(st.dz) <= 1e-5 * z && fabs(st.dv) <= 1e-5;
+  }
+  for (int it = 0; !done && it < maxit; ++it) {
     const NewtonStep<double> st = c2p_newton<double>(z, v2, q.e, q.s, q.q, q.b, g1);
     c2p_apply(z, v2, st);
     ++res.iters;

@@ -308,3 +308,170 @@ class Solver:
             self.step_cfl(cfl, t_end)
             steps += 1
         return steps
+
+
+# ------------------------------------------------------------------ ensembles of 1-D tubes
+ENSEMBLE_EXPORTED = (
+    "hz_ensemble_workspace_bytes", "hz_ensemble_create", "hz_ensemble_destroy",
+    "hz_ensemble_set_primitives", "hz_ensemble_set_launch", "hz_ensemble_run",
+    "hz_ensemble_get_primitives", "hz_ensemble_results", "hz_ensemble_autotune",
+)
+
+
+def _ens_lib():
+    L = lib()
+    if not getattr(L, "_ens_ready", False):
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        ip, dp, lp = P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_longlong)
+        L.hz_ensemble_workspace_bytes.argtypes = [ctypes.c_int, ip, P(ctypes.c_size_t)]
+        L.hz_ensemble_create.argtypes = [P(vp), ctypes.c_int, ip, dp, dp, P(hz_options), vp,
+                                         ctypes.c_size_t, vp]
+        L.hz_ensemble_destroy.argtypes = [vp]
+        L.hz_ensemble_set_primitives.argtypes = [vp, vp]
+        L.hz_ensemble_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.hz_ensemble_run.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_longlong, ctypes.c_int]
+        L.hz_ensemble_get_primitives.argtypes = [vp, vp]
+        L.hz_ensemble_results.argtypes = [vp, dp, lp, lp]
+        L.hz_ensemble_autotune.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double, ip, ip,
+                                           P(ctypes.c_float)]
+        for name in ENSEMBLE_EXPORTED:
+            getattr(L, name).restype = ctypes.c_int
+        L._ens_ready = True
+    return L
+
+
+def _iarr(x):
+    a = np.ascontiguousarray(x, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _darr(x):
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def hz_ensemble_workspace_bytes(n) -> int:
+    na, np_ = _iarr(n)
+    out = ctypes.c_size_t(0)
+    _check(_ens_lib().hz_ensemble_workspace_bytes(len(na), np_, ctypes.byref(out)),
+           "hz_ensemble_workspace_bytes")
+    return int(out.value)
+
+
+def hz_ensemble_create(n, dx, gamma, opts: hz_options, d_workspace: int, nbytes: int, stream: int) -> int:
+    na, np_ = _iarr(n)
+    da, dp_ = _darr(dx)
+    ga, gp = _darr(gamma)
+    h = ctypes.c_void_p(0)
+    _check(_ens_lib().hz_ensemble_create(ctypes.byref(h), len(na), np_, dp_, gp, ctypes.byref(opts),
+                                         ctypes.c_void_p(d_workspace), nbytes, ctypes.c_void_p(stream)),
+           "hz_ensemble_create")
+    return int(h.value)
+
+
+def hz_ensemble_destroy(ens: int) -> None:
+    _ens_lib().hz_ensemble_destroy(ctypes.c_void_p(ens))
+
+
+def hz_ensemble_set_primitives(ens: int, d_prim: int) -> None:
+    _check(_ens_lib().hz_ensemble_set_primitives(ctypes.c_void_p(ens), ctypes.c_void_p(d_prim)),
+           "hz_ensemble_set_primitives")
+
+
+def hz_ensemble_set_launch(ens: int, threads: int, ctas_per_sm: int) -> None:
+    _check(_ens_lib().hz_ensemble_set_launch(ctypes.c_void_p(ens), int(threads), int(ctas_per_sm)),
+           "hz_ensemble_set_launch")
+
+
+def hz_ensemble_run(ens: int, t_end: float, cfl: float, max_steps: int = 1 << 40, use_graph: bool = False) -> None:
+    _check(_ens_lib().hz_ensemble_run(ctypes.c_void_p(ens), float(t_end), float(cfl), int(max_steps),
+                                      int(bool(use_graph))), "hz_ensemble_run")
+
+
+def hz_ensemble_get_primitives(ens: int, d_prim: int) -> None:
+    _check(_ens_lib().hz_ensemble_get_primitives(ctypes.c_void_p(ens), ctypes.c_void_p(d_prim)),
+           "hz_ensemble_get_primitives")
+
+
+def hz_ensemble_results(ens: int, ntubes: int):
+    t = np.zeros(ntubes)
+    st = np.zeros(ntubes, dtype=np.int64)
+    fl = np.zeros(ntubes, dtype=np.int64)
+    code = _ens_lib().hz_ensemble_results(ctypes.c_void_p(ens), t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          st.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                          fl.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    if code < 0:
+        raise HznError(code, "hz_ensemble_results")
+    return t, st, fl
+
+
+def hz_ensemble_autotune(ens: int, d_prim: int, t_probe: float, cfl: float):
+    th, cps = ctypes.c_int(0), ctypes.c_int(0)
+    ms = (ctypes.c_float * 5)()
+    _check(_ens_lib().hz_ensemble_autotune(ctypes.c_void_p(ens), ctypes.c_void_p(d_prim), float(t_probe),
+                                           float(cfl), ctypes.byref(th), ctypes.byref(cps), ms),
+           "hz_ensemble_autotune")
+    return int(th.value), int(cps.value), list(ms)
+
+
+class Ensemble:
+    """Independent 1-D tubes (workloads.Problem instances along x) on the current CUDA device."""
+
+    def __init__(self, problems, rho_floor: float = 1e-12, p_floor: float = 1e-14, c2p_maxit: int = 50,
+                 c2p_tol: float = 1e-12, stream=None):
+        import torch
+
+        self.torch = torch
+        self.problems = list(problems)
+        self.n = np.array([p.n[0] for p in self.problems], dtype=np.int32)
+        dx = np.array([p.dx[0] for p in self.problems])
+        gam = np.array([p.gamma for p in self.problems])
+        self.options = make_options(2.0, rho_floor=rho_floor, p_floor=p_floor, c2p_maxit=c2p_maxit,
+                                    c2p_tol=c2p_tol)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        nbytes = hz_ensemble_workspace_bytes(self.n)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.ens = hz_ensemble_create(self.n, dx, gam, self.options, base, nbytes, self.stream.cuda_stream)
+        self.ncat = int(self.n.sum())
+        self.off = np.concatenate([[0], np.cumsum(self.n)[:-1]]).astype(np.int64)
+        host = np.zeros((9, self.ncat))
+        for p, o in zip(self.problems, self.off):
+            host[:, o:o + p.n[0]] = p.prim[:, 0, 0, :]
+        self.host_prim = host
+        self.d_prim = torch.from_numpy(host).to("cuda")
+        torch.cuda.synchronize()
+        self.set_primitives()
+
+    def close(self):
+        if getattr(self, "ens", None):
+            hz_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_primitives(self):
+        with self.torch.cuda.stream(self.stream):
+            hz_ensemble_set_primitives(self.ens, self.d_prim.data_ptr())
+
+    def autotune(self, t_probe: float = 0.02, cfl: float = 0.5):
+        return hz_ensemble_autotune(self.ens, self.d_prim.data_ptr(), t_probe, cfl)
+
+    def run(self, t_end: float, cfl: float = 0.5, use_graph: bool = True, max_steps: int = 1 << 40):
+        hz_ensemble_run(self.ens, t_end, cfl, max_steps, use_graph)
+
+    def primitives(self):
+        """List of (9, 1, 1, n) arrays, one per tube."""
+        out = self.torch.empty((9, self.ncat), dtype=self.torch.float64, device="cuda")
+        hz_ensemble_get_primitives(self.ens, out.data_ptr())
+        self.stream.synchronize()
+        h = out.cpu().numpy()
+        return [h[:, o:o + n].reshape(9, 1, 1, n).copy() for o, n in zip(self.off, self.n)]
+
+    def results(self):
+        return hz_ensemble_results(self.ens, len(self.n))

@@ -24,7 +24,7 @@ def lib():
 
 
 def test_header_declares_binding_names():
-    assert set(declared_functions()) == set(hzn.EXPORTED)
+    assert set(declared_functions()) == set(hzn.EXPORTED) | set(hzn.ENSEMBLE_EXPORTED)
 
 
 def test_library_exports_every_declared_symbol(lib):

@@ -1,0 +1,61 @@
+"""Ensembles of independent 1-D magnetised tubes in one persistent launch, against the FP64
+oracle tube by tube (relative L1 per field <= 1e-8 at the end time, the FP64 end-time bar)."""
+import numpy as np
+import pytest
+
+from parity import TOL_END, assert_parity, oracle_run
+from paper_1102_5202_gb300 import hzn
+from paper_1102_5202_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1102_5202_gb300 import build
+    build.build_library()
+    hzn.lib()
+
+
+@pytest.fixture(scope="module")
+def small_ensemble():
+    # the benchmark ensemble's distribution of states, with sizes the oracle runs in seconds
+    return W.ensemble(count=20, seed=1103, nmin=64, nmax=320, t_end=0.4)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_ensemble_matches_oracle_per_tube(small_ensemble, use_graph):
+    E = hzn.Ensemble(small_ensemble)
+    E.run(0.4, 0.5, use_graph=use_graph)
+    got = E.primitives()
+    t, steps, fails = E.results()
+    assert np.all(np.abs(t - 0.4) < 1e-14)
+    for k, P in enumerate(small_ensemble):
+        op, _, os_ = oracle_run(P, t_end=0.4, cfl=0.5)
+        assert steps[k] == os_["steps"] and fails[k] == os_["fails"], k
+        assert_parity(got[k], op, TOL_END, fields=range(8), what=f"tube {k} (n={P.n[0]})")
+
+
+def test_ensemble_graph_replay_and_autotune(small_ensemble):
+    E = hzn.Ensemble(small_ensemble)
+    E.run(0.4, 0.5, use_graph=True)
+    first = E.primitives()
+    E.set_primitives()
+    E.run(0.4, 0.5, use_graph=True)  # replays the captured graph
+    again = E.primitives()
+    for a, b in zip(first, again):
+        assert np.array_equal(a, b)
+    threads, ctas, ms = E.autotune(t_probe=0.05)
+    assert (threads, ctas) in {(64, 4), (128, 1), (128, 2), (128, 3), (256, 1)}
+    assert all(m > 0 for m in ms)
+    E.run(0.4, 0.5, use_graph=True)
+    tuned = E.primitives()
+    for a, b in zip(first, tuned):
+        assert np.array_equal(a, b)  # the launch shape does not change any tube's arithmetic
+
+
+def test_ensemble_workspace_and_errors():
+    with pytest.raises(hzn.HznError):
+        hzn.hz_ensemble_workspace_bytes([1, 5])
+    nb = hzn.hz_ensemble_workspace_bytes([200, 4000])
+    assert nb >= 4 * 9 * (224 + 4000) * 8
