@@ -73,6 +73,8 @@ def lib():
             L.hzo_prim2cons.argtypes = [ctypes.c_long, op, dp, dp, dp]
             L.hzo_cons2prim.argtypes = [ctypes.c_long, op, dp, dp, dp, dp, ip, ip]
             L.hzo_cons2prim.restype = ctypes.c_long
+            L.hzo_recover.argtypes = [ctypes.c_long, op, dp, dp, dp, dp, ip]
+            L.hzo_recover.restype = ctypes.c_long
             L.hzo_flux.argtypes = [ctypes.c_long, op, ctypes.c_int, dp, dp, dp]
             L.hzo_speeds.argtypes = [ctypes.c_long, op, ctypes.c_int, dp, dp, dp]
             L.hzo_state.argtypes = [ctypes.c_long, op, dp, dp, dp]
@@ -145,6 +147,23 @@ def cons2prim(opts: Opts, met, cons, guess=None):
                         st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                         it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     return out, st, it
+
+
+def recover(opts: Opts, met, cons, guess=None):
+    """Recovery with the step's atmosphere / cold-recovery / floor rules.
+    Returns (prim, cons_after, status)."""
+    met = _f64(met)
+    cons = _f64(cons).copy()
+    n = cons.shape[0]
+    out = np.zeros((n, 9))
+    st = np.zeros(n, dtype=np.int32)
+    g = None
+    if guess is not None:
+        guess = _f64(guess)
+        g = _dp(guess)
+    lib().hzo_recover(n, ctypes.byref(opts), _dp(met), _dp(cons), g, _dp(out),
+                      st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return out, cons, st
 
 
 def flux(opts: Opts, d: int, met, prim) -> np.ndarray:

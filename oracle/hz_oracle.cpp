@@ -26,9 +26,9 @@
 //     Psi = sqrt(gamma) psi, extra flux sqrt(-g) gamma^{dj} psi on B^j, flux
 //     sqrt(gamma)(c_h^2 alpha^2 B^d - beta^d psi) on Psi, source -kappa alpha Psi; the pair
 //     (B^d, Psi) uses HLLE bounds -beta^d -+ c_h alpha sqrt(gamma^dd);
-//   * floors: a failed recovery or rho < rho_floor resets the cell to atmosphere
-//     (rho_floor, p_atm, zero velocity, same B and psi) and recomputes its conserved vector;
-//     p < p_floor is raised to p_floor and the conserved vector is recomputed.
+//   * floors: a cell with D/sqrt(gamma) < rho_atm, a failed recovery, or a recovered
+//     rho < rho_floor is set to atmosphere (rho_floor, p_atm, zero velocity, same B and psi);
+//     p < p_floor is raised to p_floor; every reset recomputes the conserved vector.
 //
 // Numerics are compiled with -ffp-contract=off so that x86 and Arm give the same bits.
 
@@ -630,6 +630,22 @@ long hzo_cons2prim(long n, const hzo_opts* o, const double* met, const double* c
                      prim + c * NPRIM, &it);
     if (status) status[c] = s;
     if (iters) iters[c] = it;
+    nf += s;
+  }
+  return nf;
+}
+
+// Recovery with the atmosphere and floor rules of the step, pointwise.  cons is
+// rewritten when a cell is reset; status[c] = 1 when the energy-based recovery failed.
+long hzo_recover(long n, const hzo_opts* o, const double* met, double* cons, const double* guess,
+                 double* prim, int* status) {
+  long nf = 0;
+  for (long c = 0; c < n; ++c) {
+    Geom G = make_geom(met + c * NMET);
+    int it = 0;
+    const int s = recover_cell(G, cons + c * NCONS, guess ? guess + c * NPRIM : nullptr, *o,
+                               prim + c * NPRIM, &it);
+    if (status) status[c] = s;
     nf += s;
   }
   return nf;

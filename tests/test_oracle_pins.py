@@ -461,3 +461,30 @@ def test_cleaning_keeps_1d_bx_constant():
     U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
     out, Uo, *_ = O.evolve(grid, opts, P.metric, P.prim, U, 0.1, 0.5)
     assert np.all(out[5] == 0.5) and np.all(out[8] == 0.0)
+
+
+# --------------------------------------------------------------------- floors / atmosphere
+def test_failed_recovery_resets_to_atmosphere():
+    """States with an energy below the causal bound E >= |S| have no admissible root; the
+    step's recovery sets them to the atmosphere and rewrites the conserved vector to match."""
+    n = 100
+    met = W.random_metric_points(n, seed=71)
+    prim = W.random_prim_points(n, seed=72, met=met, wmax=3.0, sigma_max=1.0)
+    opts = O.make_opts(5.0 / 3.0, rho_floor=1e-9, p_floor=1e-12)
+    U = O.prim2cons(opts, met, prim)
+    s = O.state(opts, met, prim)
+    sqrtg, alp = s[:, 10], s[:, 11]
+    g = np.stack([np.stack([met[:, 4], met[:, 5], met[:, 6]], -1),
+                  np.stack([met[:, 5], met[:, 7], met[:, 8]], -1),
+                  np.stack([met[:, 6], met[:, 8], met[:, 9]], -1)], -2)
+    S = U[:, 2:5] / sqrtg[:, None]
+    Smag = np.sqrt(np.einsum("ni,nij,nj->n", S, np.linalg.inv(g), S))
+    # E = (-T_t + beta^i T_i) / (alpha sqrt(gamma)) set to 0.9 |S|
+    U[:, 1] = (met[:, 1:4] * U[:, 2:5]).sum(1) - alp * sqrtg * 0.9 * Smag
+    _, st0, _ = O.cons2prim(opts, met, U)
+    assert st0.sum() == n
+    prim2, U2, st = O.recover(opts, met, U)
+    assert st.sum() == n
+    assert np.all(prim2[:, 0] == 1e-9) and np.all(prim2[:, 2:5] == 0.0)
+    assert np.allclose(prim2[:, 5:8], U[:, 5:8] / (alp * sqrtg)[:, None], rtol=1e-14, atol=0)
+    assert np.allclose(U2, O.prim2cons(opts, met, prim2), rtol=1e-14, atol=1e-300)
