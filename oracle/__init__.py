@@ -89,6 +89,9 @@ def lib():
             L.hzo_evolve.argtypes = [gp, op, dp, dp, dp, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_long, dp, P(ctypes.c_long)]
             L.hzo_evolve.restype = ctypes.c_long
+            L.hzo_evolve_cs.argtypes = [gp, op, dp, dp, dp, ctypes.c_double, ctypes.c_long, dp, dp, dp,
+                                        dp]
+            L.hzo_evolve_cs.restype = ctypes.c_long
             L.hzo_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -150,7 +153,7 @@ def cons2prim(opts: Opts, met, cons, guess=None):
 
 
 def recover(opts: Opts, met, cons, guess=None):
-    """Recovery with the step's atmosphere / cold-recovery / floor rules.
+    """Recovery with the step's atmosphere and floor rules.
     Returns (prim, cons_after, status)."""
     met = _f64(met)
     cons = _f64(cons).copy()
@@ -246,3 +249,20 @@ def evolve(grid: Grid, opts: Opts, met, prim, cons, t_end: float, cfl: float,
                              float(t_end), float(cfl), float(fixed_dt), int(max_steps),
                              ctypes.byref(t), ctypes.byref(nf))
     return prim, cons, int(steps), float(t.value), int(nf.value)
+
+
+def evolve_cs(grid: Grid, opts: Opts, met, prim, dprim, h: float, dt: float, nsteps: int):
+    """Complex-step directional derivative of the state after nsteps fixed steps of size dt.
+
+    Runs the scheme on prim + i h dprim and returns (prim_end, dprim_end, cons_end, dcons_end,
+    failures) with dX_end = Im(X_end(prim + i h dprim)) / h: the derivative of the discrete map
+    (branch decisions frozen at the real state) up to O(h^2) and round-off, since no difference
+    of nearby values is formed."""
+    met = _f64(met)
+    pre = _f64(prim)
+    pim = _f64(dprim) * float(h)
+    ore, oim = np.empty_like(pre), np.empty_like(pre)
+    cre, cim = np.empty_like(pre), np.empty_like(pre)
+    nf = lib().hzo_evolve_cs(ctypes.byref(grid), ctypes.byref(opts), _dp(met), _dp(pre), _dp(pim),
+                             float(dt), int(nsteps), _dp(ore), _dp(oim), _dp(cre), _dp(cim))
+    return ore, oim / float(h), cre, cim / float(h), int(nf)

@@ -30,9 +30,16 @@
 //     rho < rho_floor is set to atmosphere (rho_floor, p_atm, zero velocity, same B and psi);
 //     p < p_floor is raised to p_floor; every reset recomputes the conserved vector.
 //
+// Every function is written for a scalar type R: double, or std::complex<double> for
+// complex-step differentiation (d J / d q = Im J(q + i h) / h, exact to round-off for the
+// discrete scheme with its branch decisions frozen).  Decisions (limiter, wave-speed bounds,
+// floors) use real parts; |x| is continued analytically; the recovery root found on the real
+// part is polished by complex Newton steps, which carries its derivative exactly.
+//
 // Numerics are compiled with -ffp-contract=off so that x86 and Arm give the same bits.
 
 #include <cmath>
+#include <complex>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -47,6 +54,18 @@ namespace hzo {
 enum { RHO = 0, PRS, UTX, UTY, UTZ, BCX, BCY, BCZ, PSI, NPRIM };
 enum { CD = 0, CTT, CTX, CTY, CTZ, CBX, CBY, CBZ, CPSI, NCONS };
 enum { ALP = 0, BEX, BEY, BEZ, GXX, GXY, GXZ, GYY, GYZ, GZZ, NMET };
+
+using cplx = std::complex<double>;
+
+// Real part used for every decision; |x| continued analytically; min/max by real part.
+inline double re(double x) { return x; }
+inline double re(const cplx& x) { return x.real(); }
+inline double absv(double x) { return std::fabs(x); }
+inline cplx absv(const cplx& x) { return x.real() < 0.0 ? -x : x; }
+inline double minv(double a, double b) { return std::min(a, b); }
+inline double maxv(double a, double b) { return std::max(a, b); }
+inline cplx minv(const cplx& a, const cplx& b) { return b.real() < a.real() ? b : a; }
+inline cplx maxv(const cplx& a, const cplx& b) { return a.real() < b.real() ? b : a; }
 
 }  // namespace hzo
 
@@ -79,17 +98,19 @@ namespace hzo {
 // ----------------------------------------------------------------------------------------
 // 3+1 geometry at one point: lapse alpha, shift beta^i, spatial metric gamma_ij (§2.1).
 // ----------------------------------------------------------------------------------------
+template <class R>
 struct Geom {
-  double alp, beta[3], g[3][3];
-  double ginv[3][3];   // gamma^{ij}
-  double sqrtgam;      // sqrt(det gamma_ij)
-  double sqrtmg;       // sqrt(-g) = alpha sqrt(gamma)
-  double g4[4][4];     // g_{mu nu}
-  double g4inv[4][4];  // g^{mu nu}
+  R alp, beta[3], g[3][3];
+  R ginv[3][3];   // gamma^{ij}
+  R sqrtgam;      // sqrt(det gamma_ij)
+  R sqrtmg;       // sqrt(-g) = alpha sqrt(gamma)
+  R g4[4][4];     // g_{mu nu}
+  R g4inv[4][4];  // g^{mu nu}
 };
 
-static Geom make_geom(const double m[NMET]) {
-  Geom G;
+template <class R>
+static Geom<R> make_geom(const R m[NMET]) {
+  Geom<R> G;
   G.alp = m[ALP];
   G.beta[0] = m[BEX];
   G.beta[1] = m[BEY];
@@ -101,13 +122,13 @@ static Geom make_geom(const double m[NMET]) {
   G.g[1][2] = G.g[2][1] = m[GYZ];
   G.g[2][2] = m[GZZ];
   // inverse by cofactors
-  double c00 = G.g[1][1] * G.g[2][2] - G.g[1][2] * G.g[2][1];
-  double c01 = G.g[1][2] * G.g[2][0] - G.g[1][0] * G.g[2][2];
-  double c02 = G.g[1][0] * G.g[2][1] - G.g[1][1] * G.g[2][0];
-  double det = G.g[0][0] * c00 + G.g[0][1] * c01 + G.g[0][2] * c02;
-  double c11 = G.g[0][0] * G.g[2][2] - G.g[0][2] * G.g[2][0];
-  double c12 = G.g[0][2] * G.g[1][0] - G.g[0][0] * G.g[1][2];
-  double c22 = G.g[0][0] * G.g[1][1] - G.g[0][1] * G.g[1][0];
+  R c00 = G.g[1][1] * G.g[2][2] - G.g[1][2] * G.g[2][1];
+  R c01 = G.g[1][2] * G.g[2][0] - G.g[1][0] * G.g[2][2];
+  R c02 = G.g[1][0] * G.g[2][1] - G.g[1][1] * G.g[2][0];
+  R det = G.g[0][0] * c00 + G.g[0][1] * c01 + G.g[0][2] * c02;
+  R c11 = G.g[0][0] * G.g[2][2] - G.g[0][2] * G.g[2][0];
+  R c12 = G.g[0][2] * G.g[1][0] - G.g[0][0] * G.g[1][2];
+  R c22 = G.g[0][0] * G.g[1][1] - G.g[0][1] * G.g[1][0];
   G.ginv[0][0] = c00 / det;
   G.ginv[0][1] = G.ginv[1][0] = c01 / det;
   G.ginv[0][2] = G.ginv[2][0] = c02 / det;
@@ -117,12 +138,12 @@ static Geom make_geom(const double m[NMET]) {
   G.sqrtgam = std::sqrt(det);
   G.sqrtmg = G.alp * G.sqrtgam;
   // 4-metric: g_tt = -alpha^2 + beta_k beta^k, g_ti = beta_i, g_ij = gamma_ij
-  double blow[3];
+  R blow[3];
   for (int i = 0; i < 3; ++i) {
     blow[i] = 0.0;
     for (int j = 0; j < 3; ++j) blow[i] += G.g[i][j] * G.beta[j];
   }
-  double bb = 0.0;
+  R bb = 0.0;
   for (int i = 0; i < 3; ++i) bb += blow[i] * G.beta[i];
   G.g4[0][0] = -G.alp * G.alp + bb;
   for (int i = 0; i < 3; ++i) {
@@ -130,7 +151,7 @@ static Geom make_geom(const double m[NMET]) {
     for (int j = 0; j < 3; ++j) G.g4[i + 1][j + 1] = G.g[i][j];
   }
   // inverse 4-metric: g^tt = -1/alpha^2, g^ti = beta^i/alpha^2, g^ij = gamma^ij - beta^i beta^j/alpha^2
-  double ia2 = 1.0 / (G.alp * G.alp);
+  R ia2 = 1.0 / (G.alp * G.alp);
   G.g4inv[0][0] = -ia2;
   for (int i = 0; i < 3; ++i) {
     G.g4inv[0][i + 1] = G.g4inv[i + 1][0] = G.beta[i] * ia2;
@@ -143,23 +164,25 @@ static Geom make_geom(const double m[NMET]) {
 // Fluid + field state of one primitive vector (§2.1): u^mu, b^mu, b^2, enthalpy density.
 // Primitive velocity u~^i = W v^i = u^i + W beta^i / alpha (§5.2 footnote); B^i = *F^{it}.
 // ----------------------------------------------------------------------------------------
+template <class R>
 struct State {
-  double rho, p, w;  // w = rho h = rho + gamma p / (gamma - 1)
-  double W;          // Lorentz factor
-  double u[4], ul[4];
-  double b[4], bl[4];
-  double b2;
-  double B[3];
-  double psi;
+  R rho, p, w;  // w = rho h = rho + gamma p / (gamma - 1)
+  R W;          // Lorentz factor
+  R u[4], ul[4];
+  R b[4], bl[4];
+  R b2;
+  R B[3];
+  R psi;
 };
 
-static State make_state(const Geom& G, const double P[NPRIM], double gamma) {
-  State S;
+template <class R>
+static State<R> make_state(const Geom<R>& G, const R P[NPRIM], double gamma) {
+  State<R> S;
   S.rho = P[RHO];
   S.p = P[PRS];
   S.w = S.rho + gamma / (gamma - 1.0) * S.p;
-  double ut[3] = {P[UTX], P[UTY], P[UTZ]};
-  double uu = 0.0;
+  R ut[3] = {P[UTX], P[UTY], P[UTZ]};
+  R uu = 0.0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) uu += G.g[i][j] * ut[i] * ut[j];
   S.W = std::sqrt(1.0 + uu);
@@ -185,21 +208,24 @@ static State make_state(const Geom& G, const double P[NPRIM], double gamma) {
 }
 
 // Mixed energy-momentum tensor T^mu_nu = (w + b^2) u^mu u_nu + (p + b^2/2) delta^mu_nu - b^mu b_nu.
-static double Tmix(const State& S, int mu, int nu) {
-  double t = (S.w + S.b2) * S.u[mu] * S.ul[nu] - S.b[mu] * S.bl[nu];
+template <class R>
+static R Tmix(const State<R>& S, int mu, int nu) {
+  R t = (S.w + S.b2) * S.u[mu] * S.ul[nu] - S.b[mu] * S.bl[nu];
   if (mu == nu) t += S.p + 0.5 * S.b2;
   return t;
 }
 
 // Contravariant T^{mu nu}.
-static double Tup(const Geom& G, const State& S, int mu, int nu) {
+template <class R>
+static R Tup(const Geom<R>& G, const State<R>& S, int mu, int nu) {
   return (S.w + S.b2) * S.u[mu] * S.u[nu] + (S.p + 0.5 * S.b2) * G.g4inv[mu][nu] -
          S.b[mu] * S.b[nu];
 }
 
 // Conserved vector w(u) (§2.2: algebraic, evaluated per cell): sqrt(-g) J^t, sqrt(-g) T^t_mu,
 // sqrt(-g) B^i (§2.1), plus Psi = sqrt(gamma) psi.
-static void prim2cons(const Geom& G, const State& S, double U[NCONS]) {
+template <class R>
+static void prim2cons(const Geom<R>& G, const State<R>& S, R U[NCONS]) {
   U[CD] = G.sqrtmg * S.rho * S.u[0];
   for (int nu = 0; nu < 4; ++nu) U[CTT + nu] = G.sqrtmg * Tmix(S, 0, nu);
   for (int i = 0; i < 3; ++i) U[CBX + i] = G.sqrtmg * S.B[i];
@@ -208,7 +234,8 @@ static void prim2cons(const Geom& G, const State& S, double U[NCONS]) {
 
 // Flux vector along axis d (§2.1 Eq. 2): sqrt(-g) J^d, sqrt(-g) T^d_mu,
 // sqrt(-g)(b^j u^d - b^d u^j) [+ cleaning terms].
-static void flux(const Geom& G, const State& S, int d, const hzo_opts& o, double F[NCONS]) {
+template <class R>
+static void flux(const Geom<R>& G, const State<R>& S, int d, const hzo_opts& o, R F[NCONS]) {
   const int dd = d + 1;
   F[CD] = G.sqrtmg * S.rho * S.u[dd];
   for (int nu = 0; nu < 4; ++nu) F[CTT + nu] = G.sqrtmg * Tmix(S, dd, nu);
@@ -224,38 +251,42 @@ static void flux(const Geom& G, const State& S, int d, const hzo_opts& o, double
 // Fast-magnetosonic characteristic speeds dx^d/dt: roots of
 //   (u^d - l u^t)^2 = c^2 [ g^tt l^2 - 2 g^td l + g^dd + (u^d - l u^t)^2 ],
 // c^2 = cs^2 + vA^2 - cs^2 vA^2, cs^2 = gamma p / w, vA^2 = b^2 / (w + b^2).
-static void speeds(const Geom& G, const State& S, int d, double gamma, double* lm, double* lp) {
+template <class R>
+static void speeds(const Geom<R>& G, const State<R>& S, int d, double gamma, R* lm, R* lp) {
   const int dd = d + 1;
-  double cs2 = gamma * S.p / S.w;
-  double va2 = S.b2 / (S.w + S.b2);
-  double c2 = cs2 + va2 - cs2 * va2;
-  double A = (1.0 - c2) * S.u[0] * S.u[0] - c2 * G.g4inv[0][0];
-  double B = -2.0 * ((1.0 - c2) * S.u[0] * S.u[dd] - c2 * G.g4inv[0][dd]);
-  double C = (1.0 - c2) * S.u[dd] * S.u[dd] - c2 * G.g4inv[dd][dd];
-  double disc = B * B - 4.0 * A * C;
-  if (disc < 0.0) disc = 0.0;
-  double sq = std::sqrt(disc);
+  R cs2 = gamma * S.p / S.w;
+  R va2 = S.b2 / (S.w + S.b2);
+  R c2 = cs2 + va2 - cs2 * va2;
+  R A = (1.0 - c2) * S.u[0] * S.u[0] - c2 * G.g4inv[0][0];
+  R B = -2.0 * ((1.0 - c2) * S.u[0] * S.u[dd] - c2 * G.g4inv[0][dd]);
+  R C = (1.0 - c2) * S.u[dd] * S.u[dd] - c2 * G.g4inv[dd][dd];
+  R disc = B * B - 4.0 * A * C;
+  if (re(disc) < 0.0) disc = 0.0;
+  R sq = std::sqrt(disc);
   *lp = (-B + sq) / (2.0 * A);
   *lm = (-B - sq) / (2.0 * A);
 }
 
 // Coordinate speeds of the cleaning pair (B^d, Psi): -beta^d -+ c_h alpha sqrt(gamma^dd).
-static void clean_speeds(const Geom& G, int d, double ch, double* lm, double* lp) {
-  double a = ch * G.alp * std::sqrt(G.ginv[d][d]);
+template <class R>
+static void clean_speeds(const Geom<R>& G, int d, double ch, R* lm, R* lp) {
+  R a = ch * G.alp * std::sqrt(G.ginv[d][d]);
   *lm = -G.beta[d] - a;
   *lp = -G.beta[d] + a;
 }
 
 // MC-limited slope (TVD reconstruction with the monotonized-central limiter, §3.2).
-static double mc_slope(double dm, double dp) {
-  if (dm * dp <= 0.0) return 0.0;
-  double a = std::min(std::min(2.0 * std::fabs(dm), 2.0 * std::fabs(dp)), 0.5 * std::fabs(dm + dp));
-  return dp > 0.0 ? a : -a;
+template <class R>
+static R mc_slope(const R& dm, const R& dp) {
+  if (re(dm) * re(dp) <= 0.0) return R(0.0);
+  R a = minv(minv(2.0 * absv(dm), 2.0 * absv(dp)), 0.5 * absv(dm + dp));
+  return re(dp) > 0.0 ? a : -a;
 }
 
 // HLLE flux of one component (§2.2: needs only the two fluxes and the two wave-speed bounds).
-static double hlle(double sl, double sr, double FL, double FR, double UL, double UR) {
-  if (sr - sl == 0.0) return 0.5 * (FL + FR);
+template <class R>
+static R hlle(const R& sl, const R& sr, const R& FL, const R& FR, const R& UL, const R& UR) {
+  if (re(sr - sl) == 0.0) return 0.5 * (FL + FR);
   return (sr * FL - sl * FR + sl * sr * (UR - UL)) / (sr - sl);
 }
 
@@ -268,72 +299,58 @@ static double hlle(double sl, double sr, double FL, double FR, double UL, double
 //   p   = (gamma-1)/gamma (Z (1 - v^2) - D sqrt(1 - v^2)).
 // The first line gives v^2(Z) in closed form; the second is solved for Z.
 // ----------------------------------------------------------------------------------------
+template <class R>
 struct C2PIn {
-  double D, E, S2, SB, B2;
-  double Slow[3], Bn[3];
+  R D, E, S2, SB, B2;
+  R Slow[3], Bn[3];
 };
 
-static double v2_of_Z(const C2PIn& c, double Z) {
-  double ZB = Z + c.B2;
+template <class R>
+static R v2_of_Z(const C2PIn<R>& c, const R& Z) {
+  R ZB = Z + c.B2;
   return (Z * Z * c.S2 + c.SB * c.SB * (2.0 * Z + c.B2)) / (Z * Z * ZB * ZB);
 }
 
-static double dv2_dZ(const C2PIn& c, double Z) {
-  double ZB = Z + c.B2;
-  double N = Z * Z * c.S2 + c.SB * c.SB * (2.0 * Z + c.B2);
-  double Dn = Z * Z * ZB * ZB;
-  double dN = 2.0 * Z * c.S2 + 2.0 * c.SB * c.SB;
-  double dDn = 2.0 * Z * ZB * (2.0 * Z + c.B2);
+template <class R>
+static R dv2_dZ(const C2PIn<R>& c, const R& Z) {
+  R ZB = Z + c.B2;
+  R N = Z * Z * c.S2 + c.SB * c.SB * (2.0 * Z + c.B2);
+  R Dn = Z * Z * ZB * ZB;
+  R dN = 2.0 * Z * c.S2 + 2.0 * c.SB * c.SB;
+  R dDn = 2.0 * Z * ZB * (2.0 * Z + c.B2);
   return (dN * Dn - N * dDn) / (Dn * Dn);
 }
 
-static double pres_of(const C2PIn& c, double Z, double v2, double gamma) {
-  double sq = std::sqrt(1.0 - v2);
+template <class R>
+static R pres_of(const C2PIn<R>& c, const R& Z, const R& v2, double gamma) {
+  R sq = std::sqrt(1.0 - v2);
   return (gamma - 1.0) / gamma * (Z * (1.0 - v2) - c.D * sq);
 }
 
-static double f_of_Z(const C2PIn& c, double Z, double gamma) {
-  double v2 = v2_of_Z(c, Z);
-  double p = pres_of(c, Z, v2, gamma);
+template <class R>
+static R f_of_Z(const C2PIn<R>& c, const R& Z, double gamma) {
+  R v2 = v2_of_Z(c, Z);
+  R p = pres_of(c, Z, v2, gamma);
   return Z - p + 0.5 * c.B2 * (1.0 + v2) - 0.5 * c.SB * c.SB / (Z * Z) - c.E;
 }
 
-static double df_dZ(const C2PIn& c, double Z, double gamma) {
-  double v2 = v2_of_Z(c, Z);
-  double dv2 = dv2_dZ(c, Z);
+template <class R>
+static R df_dZ(const C2PIn<R>& c, const R& Z, double gamma) {
+  R v2 = v2_of_Z(c, Z);
+  R dv2 = dv2_dZ(c, Z);
   double g1 = (gamma - 1.0) / gamma;
-  double sq = std::sqrt(1.0 - v2);
-  double dp_dZ = g1 * (1.0 - v2);
-  double dp_dv2 = g1 * (-Z + 0.5 * c.D / sq);
+  R sq = std::sqrt(1.0 - v2);
+  R dp_dZ = g1 * (1.0 - v2);
+  R dp_dv2 = g1 * (-Z + 0.5 * c.D / sq);
   return 1.0 - dp_dZ - dp_dv2 * dv2 + 0.5 * c.B2 * dv2 + c.SB * c.SB / (Z * Z * Z);
 }
 
-// Returns 0 on success, 1 on failure (no bracket, no convergence, unphysical root).
-static int con2prim(const Geom& G, const double U[NCONS], const double Pguess[NPRIM],
-                    const hzo_opts& o, double P[NPRIM], int* iters) {
-  C2PIn c;
-  double isg = 1.0 / G.sqrtgam;
-  c.D = U[CD] * isg;
-  for (int i = 0; i < 3; ++i) {
-    c.Slow[i] = U[CTX + i] * isg;
-    c.Bn[i] = U[CBX + i] * isg;
-  }
-  double bS = 0.0;
-  for (int i = 0; i < 3; ++i) bS += G.beta[i] * U[CTX + i];
-  c.E = (-U[CTT] + bS) / (G.alp * G.sqrtgam);
-  c.S2 = 0.0;
-  c.B2 = 0.0;
-  c.SB = 0.0;
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      c.S2 += G.ginv[i][j] * c.Slow[i] * c.Slow[j];
-      c.B2 += G.g[i][j] * c.Bn[i] * c.Bn[j];
-    }
-  for (int i = 0; i < 3; ++i) c.SB += c.Slow[i] * c.Bn[i];
+// Bracketed root of the energy equation for real data.  Returns 0 and the root in *Zout, or 1
+// on failure (no bracket, no convergence).
+static int solve_Z(const C2PIn<double>& c, double Zg, const hzo_opts& o, double* Zout, int* iters) {
   const double gamma = o.gamma;
   *iters = 0;
   if (!(c.D > 0.0) || !(c.E > 0.0)) return 1;
-
   // Upper bound: E >= Z - p >= Z / gamma, so Z <= gamma E.
   double Zhi = gamma * c.E;
   const double v2cap = 1.0 - 1e-12;
@@ -355,11 +372,6 @@ static int con2prim(const Geom& G, const double U[NCONS], const double Pguess[NP
   if (fhi == 0.0) Zlo = Zhi;
 
   // Bisection-safeguarded Newton (the 'rtsafe' scheme of Press et al., Numerical Recipes).
-  double Zg = Pguess ? 0.0 : -1.0;
-  if (Pguess) {
-    State Sg = make_state(G, Pguess, gamma);
-    Zg = Sg.w * Sg.W * Sg.W;
-  }
   double Z = (Zg > Zlo && Zg < Zhi) ? Zg : 0.5 * (Zlo + Zhi);
   double lo = Zlo, hi = Zhi;
   int it;
@@ -376,13 +388,65 @@ static int con2prim(const Geom& G, const double U[NCONS], const double Pguess[NP
   }
   *iters = it + 1;
   if (!conv) return 1;
+  *Zout = Z;
+  return 0;
+}
 
-  double v2 = v2_of_Z(c, Z);
-  if (!(v2 < 1.0) || !(Z > 0.0)) return 1;
-  double W = 1.0 / std::sqrt(1.0 - v2);
-  double p = pres_of(c, Z, v2, gamma);
+// Newton polish of the root for complex data (the real part is already the root): the
+// imaginary part converges to the implicit-function derivative.  Nothing to do for double.
+static void polish_Z(const C2PIn<double>&, double&, double) {}
+static void polish_Z(const C2PIn<cplx>& c, cplx& Z, double gamma) {
+  for (int k = 0; k < 4; ++k) Z = Z - f_of_Z(c, Z, gamma) / df_dZ(c, Z, gamma);
+}
+
+// Returns 0 on success, 1 on failure (no bracket, no convergence, unphysical root).
+template <class R>
+static int con2prim(const Geom<R>& G, const R U[NCONS], const R Pguess[NPRIM],
+                    const hzo_opts& o, R P[NPRIM], int* iters) {
+  C2PIn<R> c;
+  R isg = 1.0 / G.sqrtgam;
+  c.D = U[CD] * isg;
+  for (int i = 0; i < 3; ++i) {
+    c.Slow[i] = U[CTX + i] * isg;
+    c.Bn[i] = U[CBX + i] * isg;
+  }
+  R bS = 0.0;
+  for (int i = 0; i < 3; ++i) bS += G.beta[i] * U[CTX + i];
+  c.E = (-U[CTT] + bS) / (G.alp * G.sqrtgam);
+  c.S2 = 0.0;
+  c.B2 = 0.0;
+  c.SB = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      c.S2 += G.ginv[i][j] * c.Slow[i] * c.Slow[j];
+      c.B2 += G.g[i][j] * c.Bn[i] * c.Bn[j];
+    }
+  for (int i = 0; i < 3; ++i) c.SB += c.Slow[i] * c.Bn[i];
+  const double gamma = o.gamma;
+
+  // root of the real part, then (complex step only) Newton polish
+  C2PIn<double> cr;
+  cr.D = re(c.D);
+  cr.E = re(c.E);
+  cr.S2 = re(c.S2);
+  cr.SB = re(c.SB);
+  cr.B2 = re(c.B2);
+  double Zg = -1.0;
+  if (Pguess) {
+    State<R> Sg = make_state(G, Pguess, gamma);
+    Zg = re(Sg.w * Sg.W * Sg.W);
+  }
+  double Zr = 0.0;
+  if (solve_Z(cr, Zg, o, &Zr, iters)) return 1;
+  R Z = Zr;
+  polish_Z(c, Z, gamma);
+
+  R v2 = v2_of_Z(c, Z);
+  if (!(re(v2) < 1.0) || !(re(Z) > 0.0)) return 1;
+  R W = 1.0 / std::sqrt(1.0 - v2);
+  R p = pres_of(c, Z, v2, gamma);
   // v^i = (S^i + (S.Bn / Z) Bn^i) / (Z + Bn^2)
-  double Sup[3];
+  R Sup[3];
   for (int i = 0; i < 3; ++i) {
     Sup[i] = 0.0;
     for (int j = 0; j < 3; ++j) Sup[i] += G.ginv[i][j] * c.Slow[j];
@@ -390,7 +454,7 @@ static int con2prim(const Geom& G, const double U[NCONS], const double Pguess[NP
   P[RHO] = c.D / W;
   P[PRS] = p;
   for (int i = 0; i < 3; ++i) {
-    double vi = (Sup[i] + c.SB / Z * c.Bn[i]) / (Z + c.B2);
+    R vi = (Sup[i] + c.SB / Z * c.Bn[i]) / (Z + c.B2);
     P[UTX + i] = W * vi;
     P[BCX + i] = c.Bn[i] / G.alp;
   }
@@ -399,30 +463,32 @@ static int con2prim(const Geom& G, const double U[NCONS], const double Pguess[NP
 }
 
 // Recovery plus atmosphere / floor treatment; may rewrite U.  Returns 1 if the cell was reset.
-static int recover_cell(const Geom& G, double U[NCONS], const double Pguess[NPRIM],
-                        const hzo_opts& o, double P[NPRIM], int* iters) {
+template <class R>
+static int recover_cell(const Geom<R>& G, R U[NCONS], const R Pguess[NPRIM], const hzo_opts& o,
+                        R P[NPRIM], int* iters) {
   // atmosphere: a cell whose rest-mass density D / sqrt(gamma) = rho W is below rho_atm is
   // not recovered but set to the atmosphere state (the decision uses the conserved state only)
-  const bool atm = o.rho_atm > 0.0 && U[CD] / G.sqrtgam < o.rho_atm;
+  const bool atm = o.rho_atm > 0.0 && re(U[CD] / G.sqrtgam) < o.rho_atm;
   int fail = 0;
   *iters = 0;
   if (!atm) fail = con2prim(G, U, Pguess, o, P, iters);
   int reset = 0;
-  if (atm || fail || P[RHO] < o.rho_floor) {
-    double Bkeep[3] = {U[CBX] / G.sqrtmg, U[CBY] / G.sqrtmg, U[CBZ] / G.sqrtmg};
+  if (atm || fail || re(P[RHO]) < o.rho_floor) {
+    R Bkeep[3] = {U[CBX] / G.sqrtmg, U[CBY] / G.sqrtmg, U[CBZ] / G.sqrtmg};
     P[RHO] = o.rho_floor;
-    P[PRS] = o.atm_K > 0.0 ? o.atm_K * std::pow(o.rho_floor, o.gamma) : o.p_floor;
-    if (P[PRS] < o.p_floor) P[PRS] = o.p_floor;
+    double patm = o.atm_K > 0.0 ? o.atm_K * std::pow(o.rho_floor, o.gamma) : o.p_floor;
+    if (patm < o.p_floor) patm = o.p_floor;
+    P[PRS] = patm;
     P[UTX] = P[UTY] = P[UTZ] = 0.0;
     for (int i = 0; i < 3; ++i) P[BCX + i] = Bkeep[i];
     P[PSI] = U[CPSI] / G.sqrtgam;
     reset = 1;
-  } else if (P[PRS] < o.p_floor) {
+  } else if (re(P[PRS]) < o.p_floor) {
     P[PRS] = o.p_floor;
     reset = 1;
   }
   if (reset) {
-    State S = make_state(G, P, o.gamma);
+    State<R> S = make_state(G, P, o.gamma);
     prim2cons(G, S, U);
   }
   return fail;
@@ -465,15 +531,17 @@ struct Mesh {
   long nmet() const { return (long)nm[0] * nm[1] * nm[2]; }
 };
 
-static void load_metric(const Mesh& M, const double* met, long mc, double m[NMET]) {
+template <class R>
+static void load_metric(const Mesh& M, const double* met, long mc, R m[NMET]) {
   const long nmt = M.nmet();
   for (int f = 0; f < NMET; ++f) m[f] = met[f * nmt + mc];
 }
 
 // Ghost fill (outflow = copy of the nearest interior cell; periodic = wrap), axis by axis.
-static void fill_ghosts(const Mesh& M, const double* prim, std::vector<double>& Pp) {
+template <class R>
+static void fill_ghosts(const Mesh& M, const R* prim, std::vector<R>& Pp) {
   const long npd = M.npad();
-  Pp.assign((size_t)npd * NPRIM, 0.0);
+  Pp.assign((size_t)npd * NPRIM, R(0.0));
   const int* n = M.g.n;
   for (int k = -M.gp[2]; k < n[2] + M.gp[2]; ++k)
     for (int j = -M.gp[1]; j < n[1] + M.gp[1]; ++j)
@@ -493,12 +561,13 @@ static void fill_ghosts(const Mesh& M, const double* prim, std::vector<double>& 
 
 // Spatial operator L(U) = - sum_d (F_{d,i+1/2} - F_{d,i-1/2}) / dx_d + S (§2.2), from the
 // primitive state.  The result is stored in L[f * ncell + cell].
-static void rhs(const Mesh& M, const hzo_opts& o, const double* met, const double* prim,
-                std::vector<double>& L) {
+template <class R>
+static void rhs(const Mesh& M, const hzo_opts& o, const double* met, const R* prim,
+                std::vector<R>& L) {
   const int* n = M.g.n;
   const long nc = M.ncell;
-  L.assign((size_t)nc * NCONS, 0.0);
-  std::vector<double> Pp;
+  L.assign((size_t)nc * NCONS, R(0.0));
+  std::vector<R> Pp;
   fill_ghosts(M, prim, Pp);
   const long npd = M.npad();
 
@@ -509,46 +578,46 @@ static void rhs(const Mesh& M, const hzo_opts& o, const double* met, const doubl
     int nf[3] = {n[0], n[1], n[2]};
     nf[d] += 1;  // faces i - 1/2 for i = 0 .. n_d
     long nfaces = (long)nf[0] * nf[1] * nf[2];
-    std::vector<double> Ff((size_t)nfaces * NCONS);
+    std::vector<R> Ff((size_t)nfaces * NCONS);
 #pragma omp parallel for schedule(static)
     for (long fidx = 0; fidx < nfaces; ++fidx) {
       int i = (int)(fidx % nf[0]);
       int j = (int)((fidx / nf[0]) % nf[1]);
       int k = (int)(fidx / ((long)nf[0] * nf[1]));
       // face between cell c-1 and c along d, c = (i,j,k)
-      double PL[NPRIM], PR[NPRIM];
+      R PL[NPRIM], PR[NPRIM];
       for (int f = 0; f < NPRIM; ++f) {
         auto at = [&](int s) {
           return Pp[(size_t)f * npd + M.pcell(i + s * e[0], j + s * e[1], k + s * e[2])];
         };
-        double pm2 = at(-2), pm1 = at(-1), p0 = at(0), pp1 = at(1);
-        double sigL = mc_slope(pm1 - pm2, p0 - pm1);  // slope in cell c-1
-        double sigR = mc_slope(p0 - pm1, pp1 - p0);   // slope in cell c
+        R pm2 = at(-2), pm1 = at(-1), p0 = at(0), pp1 = at(1);
+        R sigL = mc_slope(pm1 - pm2, p0 - pm1);  // slope in cell c-1
+        R sigR = mc_slope(p0 - pm1, pp1 - p0);   // slope in cell c
         PL[f] = pm1 + 0.5 * sigL;
         PR[f] = p0 - 0.5 * sigR;
       }
-      double mA[NMET], mB[NMET], mf[NMET];
+      R mA[NMET], mB[NMET], mf[NMET];
       load_metric(M, met, M.mcell(i - e[0], j - e[1], k - e[2]), mA);
       load_metric(M, met, M.mcell(i, j, k), mB);
       for (int f = 0; f < NMET; ++f) mf[f] = 0.5 * (mA[f] + mB[f]);
-      Geom G = make_geom(mf);
-      State SL = make_state(G, PL, o.gamma), SR = make_state(G, PR, o.gamma);
-      double FL[NCONS], FR[NCONS], UL[NCONS], UR[NCONS];
+      Geom<R> G = make_geom(mf);
+      State<R> SL = make_state(G, PL, o.gamma), SR = make_state(G, PR, o.gamma);
+      R FL[NCONS], FR[NCONS], UL[NCONS], UR[NCONS];
       flux(G, SL, d, o, FL);
       flux(G, SR, d, o, FR);
       prim2cons(G, SL, UL);
       prim2cons(G, SR, UR);
-      double lmL, lpL, lmR, lpR;
+      R lmL, lpL, lmR, lpR;
       speeds(G, SL, d, o.gamma, &lmL, &lpL);
       speeds(G, SR, d, o.gamma, &lmR, &lpR);
-      double sl = std::min(0.0, std::min(lmL, lmR));
-      double sr = std::max(0.0, std::max(lpL, lpR));
-      double* out = &Ff[(size_t)fidx * NCONS];
+      R sl = minv(R(0.0), minv(lmL, lmR));
+      R sr = maxv(R(0.0), maxv(lpL, lpR));
+      R* out = &Ff[(size_t)fidx * NCONS];
       for (int q = 0; q < NCONS; ++q) out[q] = hlle(sl, sr, FL[q], FR[q], UL[q], UR[q]);
       if (o.cleaning) {
-        double cm, cp;
+        R cm, cp;
         clean_speeds(G, d, o.ch, &cm, &cp);
-        double csl = std::min(0.0, cm), csr = std::max(0.0, cp);
+        R csl = minv(R(0.0), cm), csr = maxv(R(0.0), cp);
         out[CBX + d] = hlle(csl, csr, FL[CBX + d], FR[CBX + d], UL[CBX + d], UR[CBX + d]);
         out[CPSI] = hlle(csl, csr, FL[CPSI], FR[CPSI], UL[CPSI], UR[CPSI]);
       }
@@ -574,33 +643,93 @@ static void rhs(const Mesh& M, const hzo_opts& o, const double* met, const doubl
     int i = (int)(c % n[0]);
     int j = (int)((c / n[0]) % n[1]);
     int k = (int)(c / ((long)n[0] * n[1]));
-    double m0[NMET];
+    R m0[NMET];
     load_metric(M, met, M.mcell(i, j, k), m0);
-    Geom G = make_geom(m0);
-    double P[NPRIM];
+    Geom<R> G = make_geom(m0);
+    R P[NPRIM];
     for (int f = 0; f < NPRIM; ++f) P[f] = prim[(size_t)f * nc + c];
-    State S = make_state(G, P, o.gamma);
+    State<R> S = make_state(G, P, o.gamma);
     for (int d = 0; d < 3; ++d) {
       if (!M.act[d]) continue;
       int e[3] = {0, 0, 0};
       e[d] = 1;
-      double mp[NMET], mm[NMET];
+      R mp[NMET], mm[NMET];
       load_metric(M, met, M.mcell(i + e[0], j + e[1], k + e[2]), mp);
       load_metric(M, met, M.mcell(i - e[0], j - e[1], k - e[2]), mm);
-      Geom Gp = make_geom(mp), Gm = make_geom(mm);
-      double src = 0.0;
+      Geom<R> Gp = make_geom(mp), Gm = make_geom(mm);
+      R src = 0.0;
       for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b) {
-          double dg = (Gp.g4[a][b] - Gm.g4[a][b]) / (2.0 * M.g.dx[d]);
+          R dg = (Gp.g4[a][b] - Gm.g4[a][b]) / (2.0 * M.g.dx[d]);
           src += Tup(G, S, a, b) * dg;
         }
       L[(size_t)(CTX + d) * nc + c] += 0.5 * G.sqrtmg * src;
     }
     if (o.cleaning) {
-      double Psi = G.sqrtgam * S.psi;
+      R Psi = G.sqrtgam * S.psi;
       L[(size_t)CPSI * nc + c] += -o.kappa * G.alp * Psi;
     }
   }
+}
+
+// Conserved state of the grid from its primitive state.
+template <class R>
+static void grid_prim2cons(const Mesh& M, const hzo_opts& o, const double* met, const R* prim, R* cons) {
+  const long nc = M.ncell;
+  const int* n = M.g.n;
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < nc; ++c) {
+    int i = (int)(c % n[0]);
+    int j = (int)((c / n[0]) % n[1]);
+    int k = (int)(c / ((long)n[0] * n[1]));
+    R m[NMET], P[NPRIM], U[NCONS];
+    load_metric(M, met, M.mcell(i, j, k), m);
+    for (int f = 0; f < NPRIM; ++f) P[f] = prim[(size_t)f * nc + c];
+    Geom<R> G = make_geom(m);
+    State<R> S = make_state(G, P, o.gamma);
+    prim2cons(G, S, U);
+    for (int f = 0; f < NCONS; ++f) cons[(size_t)f * nc + c] = U[f];
+  }
+}
+
+// One Shu-Osher RK3 step of size dt (§3.2) on (prim, cons); returns the recovery failures.
+template <class R>
+static long step(const Mesh& M, const hzo_opts& o, const double* met, R* prim, R* cons, double dt) {
+  const long nc = M.ncell;
+  const int* n = M.g.n;
+  const size_t N = (size_t)nc * NCONS;
+  std::vector<R> U0(cons, cons + N), U1(N), L;
+  std::vector<R> P(prim, prim + (size_t)nc * NPRIM);
+  long fails = 0;
+  for (int stage = 0; stage < 3; ++stage) {
+    rhs(M, o, met, P.data(), L);
+    // U^(1) = U0 + dt L(U0);  U^(2) = 3/4 U0 + 1/4 (U1 + dt L(U1));  U^(3) = 1/3 U0 + 2/3 (U2 + dt L(U2))
+    for (size_t q = 0; q < N; ++q) {
+      if (stage == 0) U1[q] = U0[q] + dt * L[q];
+      else if (stage == 1) U1[q] = 0.75 * U0[q] + 0.25 * (U1[q] + dt * L[q]);
+      else U1[q] = (1.0 / 3.0) * U0[q] + (2.0 / 3.0) * (U1[q] + dt * L[q]);
+    }
+    long sf = 0;
+#pragma omp parallel for schedule(static) reduction(+ : sf)
+    for (long c = 0; c < nc; ++c) {
+      int i = (int)(c % n[0]);
+      int j = (int)((c / n[0]) % n[1]);
+      int k = (int)(c / ((long)n[0] * n[1]));
+      R m[NMET], U[NCONS], Pg[NPRIM], Pn[NPRIM];
+      load_metric(M, met, M.mcell(i, j, k), m);
+      Geom<R> G = make_geom(m);
+      for (int f = 0; f < NCONS; ++f) U[f] = U1[(size_t)f * nc + c];
+      for (int f = 0; f < NPRIM; ++f) Pg[f] = P[(size_t)f * nc + c];
+      int it;
+      sf += recover_cell(G, U, Pg, o, Pn, &it);
+      for (int f = 0; f < NCONS; ++f) U1[(size_t)f * nc + c] = U[f];
+      for (int f = 0; f < NPRIM; ++f) P[(size_t)f * nc + c] = Pn[f];
+    }
+    fails += sf;
+  }
+  std::copy(P.begin(), P.end(), prim);
+  std::copy(U1.begin(), U1.end(), cons);
+  return fails;
 }
 
 }  // namespace hzo
@@ -612,8 +741,8 @@ extern "C" {
 // Conserved vector of n pointwise states.  met: n x 10, prim: n x 9, cons: n x 9 (row-major).
 void hzo_prim2cons(long n, const hzo_opts* o, const double* met, const double* prim, double* cons) {
   for (long c = 0; c < n; ++c) {
-    Geom G = make_geom(met + c * NMET);
-    State S = make_state(G, prim + c * NPRIM, o->gamma);
+    Geom<double> G = make_geom(met + c * NMET);
+    State<double> S = make_state(G, prim + c * NPRIM, o->gamma);
     prim2cons(G, S, cons + c * NCONS);
   }
 }
@@ -624,7 +753,7 @@ long hzo_cons2prim(long n, const hzo_opts* o, const double* met, const double* c
                    const double* guess, double* prim, int* status, int* iters) {
   long nf = 0;
   for (long c = 0; c < n; ++c) {
-    Geom G = make_geom(met + c * NMET);
+    Geom<double> G = make_geom(met + c * NMET);
     int it = 0;
     int s = con2prim(G, cons + c * NCONS, guess ? guess + c * NPRIM : nullptr, *o,
                      prim + c * NPRIM, &it);
@@ -641,7 +770,7 @@ long hzo_recover(long n, const hzo_opts* o, const double* met, double* cons, con
                  double* prim, int* status) {
   long nf = 0;
   for (long c = 0; c < n; ++c) {
-    Geom G = make_geom(met + c * NMET);
+    Geom<double> G = make_geom(met + c * NMET);
     int it = 0;
     const int s = recover_cell(G, cons + c * NCONS, guess ? guess + c * NPRIM : nullptr, *o,
                                prim + c * NPRIM, &it);
@@ -654,16 +783,16 @@ long hzo_recover(long n, const hzo_opts* o, const double* met, double* cons, con
 // Pointwise flux along d, and characteristic speeds (lam: n x 2 = [minus, plus]).
 void hzo_flux(long n, const hzo_opts* o, int d, const double* met, const double* prim, double* F) {
   for (long c = 0; c < n; ++c) {
-    Geom G = make_geom(met + c * NMET);
-    State S = make_state(G, prim + c * NPRIM, o->gamma);
+    Geom<double> G = make_geom(met + c * NMET);
+    State<double> S = make_state(G, prim + c * NPRIM, o->gamma);
     flux(G, S, d, *o, F + c * NCONS);
   }
 }
 
 void hzo_speeds(long n, const hzo_opts* o, int d, const double* met, const double* prim, double* lam) {
   for (long c = 0; c < n; ++c) {
-    Geom G = make_geom(met + c * NMET);
-    State S = make_state(G, prim + c * NPRIM, o->gamma);
+    Geom<double> G = make_geom(met + c * NMET);
+    State<double> S = make_state(G, prim + c * NPRIM, o->gamma);
     speeds(G, S, d, o->gamma, lam + 2 * c, lam + 2 * c + 1);
   }
 }
@@ -672,8 +801,8 @@ void hzo_speeds(long n, const hzo_opts* o, int d, const double* met, const doubl
 // sqrt(gamma), alpha, T^t_t, w.
 void hzo_state(long n, const hzo_opts* o, const double* met, const double* prim, double* out) {
   for (long c = 0; c < n; ++c) {
-    Geom G = make_geom(met + c * NMET);
-    State S = make_state(G, prim + c * NPRIM, o->gamma);
+    Geom<double> G = make_geom(met + c * NMET);
+    State<double> S = make_state(G, prim + c * NPRIM, o->gamma);
     double* r = out + c * 14;
     for (int m = 0; m < 4; ++m) { r[m] = S.u[m]; r[4 + m] = S.b[m]; }
     r[8] = S.b2; r[9] = S.W; r[10] = G.sqrtgam; r[11] = G.alp; r[12] = Tmix(S, 0, 0); r[13] = S.w;
@@ -685,8 +814,8 @@ void hzo_state(long n, const hzo_opts* o, const double* met, const double* prim,
 void hzo_source_pointwise(long n, const hzo_opts* o, const double* met, const double* dg,
                           const double* prim, double* src) {
   for (long c = 0; c < n; ++c) {
-    Geom G = make_geom(met + c * NMET);
-    State S = make_state(G, prim + c * NPRIM, o->gamma);
+    Geom<double> G = make_geom(met + c * NMET);
+    State<double> S = make_state(G, prim + c * NPRIM, o->gamma);
     src[c * 4 + 0] = 0.0;
     for (int d = 0; d < 3; ++d) {
       double s = 0.0;
@@ -701,8 +830,8 @@ void hzo_source_pointwise(long n, const hzo_opts* o, const double* met, const do
 void hzo_tensors(long n, const hzo_opts* o, const double* met, const double* prim, double* Tuu,
                  double* g4, double* g4inv) {
   for (long c = 0; c < n; ++c) {
-    Geom G = make_geom(met + c * NMET);
-    State S = make_state(G, prim + c * NPRIM, o->gamma);
+    Geom<double> G = make_geom(met + c * NMET);
+    State<double> S = make_state(G, prim + c * NPRIM, o->gamma);
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) {
         Tuu[c * 16 + a * 4 + b] = Tup(G, S, a, b);
@@ -716,20 +845,7 @@ void hzo_tensors(long n, const hzo_opts* o, const double* met, const double* pri
 void hzo_grid_prim2cons(const hzo_grid* g, const hzo_opts* o, const double* met, const double* prim,
                         double* cons) {
   Mesh M(*g);
-  const long nc = M.ncell;
-#pragma omp parallel for schedule(static)
-  for (long c = 0; c < nc; ++c) {
-    int i = (int)(c % g->n[0]);
-    int j = (int)((c / g->n[0]) % g->n[1]);
-    int k = (int)(c / ((long)g->n[0] * g->n[1]));
-    double m[NMET], P[NPRIM], U[NCONS];
-    load_metric(M, met, M.mcell(i, j, k), m);
-    for (int f = 0; f < NPRIM; ++f) P[f] = prim[(size_t)f * nc + c];
-    Geom G = make_geom(m);
-    State S = make_state(G, P, o->gamma);
-    prim2cons(G, S, U);
-    for (int f = 0; f < NCONS; ++f) cons[(size_t)f * nc + c] = U[f];
-  }
+  grid_prim2cons(M, *o, met, prim, cons);
 }
 
 // Spatial operator L on the grid (field-major), for tests.
@@ -753,8 +869,8 @@ double hzo_max_speed(const hzo_grid* g, const hzo_opts* o, const double* met, co
     double m[NMET], P[NPRIM];
     load_metric(M, met, M.mcell(i, j, k), m);
     for (int f = 0; f < NPRIM; ++f) P[f] = prim[(size_t)f * nc + c];
-    Geom G = make_geom(m);
-    State S = make_state(G, P, o->gamma);
+    Geom<double> G = make_geom(m);
+    State<double> S = make_state(G, P, o->gamma);
     for (int d = 0; d < 3; ++d) {
       if (!M.act[d]) continue;
       double lm, lp;
@@ -778,41 +894,7 @@ double hzo_max_speed(const hzo_grid* g, const hzo_opts* o, const double* met, co
 long hzo_step(const hzo_grid* g, const hzo_opts* o, const double* met, double* prim, double* cons,
               double dt) {
   Mesh M(*g);
-  const long nc = M.ncell;
-  const size_t N = (size_t)nc * NCONS;
-  std::vector<double> U0(cons, cons + N), U1(N), L;
-  std::vector<double> P((size_t)nc * NPRIM);
-  std::memcpy(P.data(), prim, sizeof(double) * P.size());
-  long fails = 0;
-  for (int stage = 0; stage < 3; ++stage) {
-    rhs(M, *o, met, P.data(), L);
-    // U^(1) = U0 + dt L(U0);  U^(2) = 3/4 U0 + 1/4 (U1 + dt L(U1));  U^(3) = 1/3 U0 + 2/3 (U2 + dt L(U2))
-    for (size_t q = 0; q < N; ++q) {
-      if (stage == 0) U1[q] = U0[q] + dt * L[q];
-      else if (stage == 1) U1[q] = 0.75 * U0[q] + 0.25 * (U1[q] + dt * L[q]);
-      else U1[q] = (1.0 / 3.0) * U0[q] + (2.0 / 3.0) * (U1[q] + dt * L[q]);
-    }
-    long sf = 0;
-#pragma omp parallel for schedule(static) reduction(+ : sf)
-    for (long c = 0; c < nc; ++c) {
-      int i = (int)(c % g->n[0]);
-      int j = (int)((c / g->n[0]) % g->n[1]);
-      int k = (int)(c / ((long)g->n[0] * g->n[1]));
-      double m[NMET], U[NCONS], Pg[NPRIM], Pn[NPRIM];
-      load_metric(M, met, M.mcell(i, j, k), m);
-      Geom G = make_geom(m);
-      for (int f = 0; f < NCONS; ++f) U[f] = U1[(size_t)f * nc + c];
-      for (int f = 0; f < NPRIM; ++f) Pg[f] = P[(size_t)f * nc + c];
-      int it;
-      sf += recover_cell(G, U, Pg, *o, Pn, &it);
-      for (int f = 0; f < NCONS; ++f) U1[(size_t)f * nc + c] = U[f];
-      for (int f = 0; f < NPRIM; ++f) P[(size_t)f * nc + c] = Pn[f];
-    }
-    fails += sf;
-  }
-  std::memcpy(prim, P.data(), sizeof(double) * P.size());
-  std::memcpy(cons, U1.data(), sizeof(double) * N);
-  return fails;
+  return step(M, *o, met, prim, cons, dt);
 }
 
 // Evolve to t_end with dt = cfl / max_speed (the last step clipped to t_end), or with the
@@ -833,6 +915,29 @@ long hzo_evolve(const hzo_grid* g, const hzo_opts* o, const double* met, double*
   if (t_out) *t_out = t;
   if (fails_out) *fails_out = fails;
   return steps;
+}
+
+// Complex-step run: nsteps fixed-size steps from the complex primitive state
+// prim_re + i prim_im (field-major, n_cell each); the final primitive state is written to
+// out_re + i out_im and, when cons_re / cons_im are not null, the final conserved state
+// there.  Returns the recovery failures.
+long hzo_evolve_cs(const hzo_grid* g, const hzo_opts* o, const double* met, const double* prim_re,
+                   const double* prim_im, double dt, long nsteps, double* out_re, double* out_im,
+                   double* cons_re, double* cons_im) {
+  Mesh M(*g);
+  const size_t N = (size_t)M.ncell * NPRIM;
+  std::vector<cplx> P(N), U(N);
+  for (size_t q = 0; q < N; ++q) P[q] = cplx(prim_re[q], prim_im[q]);
+  grid_prim2cons(M, *o, met, P.data(), U.data());
+  long fails = 0;
+  for (long s = 0; s < nsteps; ++s) fails += step(M, *o, met, P.data(), U.data(), dt);
+  for (size_t q = 0; q < N; ++q) {
+    out_re[q] = P[q].real();
+    out_im[q] = P[q].imag();
+    if (cons_re) cons_re[q] = U[q].real();
+    if (cons_im) cons_im[q] = U[q].imag();
+  }
+  return fails;
 }
 
 int hzo_num_threads(void) {
