@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--ensemble-tubes", type=int, default=512)
     ap.add_argument("--n-mixed", type=int, default=384, help="cells per axis of the mixed line")
     return ap.parse_args()
@@ -232,6 +233,10 @@ def run_gpu(args, rank, world, local):
     if not args.no_ensemble:
         ensemble = run_ensemble(args, dist, local)
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(args, dist, local)
+
     line = None
     if rank == 0:
         cpu = None
@@ -251,6 +256,7 @@ def run_gpu(args, rank, world, local):
             "e2e": e2e,
             "mixed": mixed,
             "ensemble": ensemble,
+            "adjoint": adjoint,
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "c2p_failures": int(st.c2p_failures),
@@ -306,6 +312,61 @@ def run_mixed(args, dist, local, hbm_peak):
                              "unit": "GB/s", "frac": ach / hbm_peak,
                              "roofline_zu_per_s": hbm_peak * 1e9 / HBM_BYTES_PER_ZU_MIXED},
             "c2p_failures": int(st.c2p_failures), "gpu_launches": 4 * args.steps}
+
+
+def run_adjoint(args, dist, local, reps: int = 3):
+    """The gradient configurations: the 1-D tube (N=800, 1000 fixed steps, textured base point)
+    and the 2-D cylindrical blast wave (256^2, 200 fixed steps).  Each rep times, with CUDA
+    events on the solver's stream: the plain forward run (hz_step x n), the forward pass with
+    sqrt(n) checkpoints (hz_adjoint_forward) and the reverse sweep (hz_adjoint_backward, which
+    recomputes each segment).  adjoint_over_forward = reverse sweep / plain forward (median of
+    the reps)."""
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+    from paper_1102_5202_gb300 import workloads as W
+
+    out = {}
+    for P in (W.adjoint_tube(800), W.blast2d(256)):
+        steps, dt = P.steps, W.fixed_dt(P)
+        s = hzn.Solver.for_problem(P)
+        A = hzn.Adjoint(s, steps, dt)
+        st = s.stream
+        g = torch.zeros((9,) + P.prim.shape[1:], dtype=torch.float64, device="cuda")
+        g[0] = 1.0
+        prim0 = s._dev(P.prim)
+        rows = []
+        for rep in range(reps + 1):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            torch.cuda.synchronize()
+            with torch.cuda.stream(st):
+                s.set_primitives(prim0)
+                ev[0].record(st)
+                for _ in range(steps):
+                    s.step(dt)
+                ev[1].record(st)
+                A.forward(prim0)
+                ev[2].record(st)
+                A.backward(g)
+                ev[3].record(st)
+            ev[3].synchronize()
+            if rep:  # the first rep warms up
+                rows.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+        rows = np.array(rows)
+        fwd, ckf, bwd = (float(np.median(rows[:, k])) for k in range(3))
+        zu = float(P.ncell) * steps
+        units, seconds = aggregate(zu, bwd * 1e-3, dist, device=torch.device("cuda", local))
+        key = "tube1d" if P.n[1] == 1 else "blast2d"
+        out[key] = {"workload": f"{P.name}_{'x'.join(str(k) for k in P.n if k > 1)}_{steps}steps_fp64",
+                    "cells": P.ncell, "steps": steps, "dt": dt, "checkpoint_every": A.checkpoint_every,
+                    "segments": A.segments, "forward_ms": fwd, "forward_checkpointed_ms": ckf,
+                    "backward_ms": bwd, "adjoint_over_forward": bwd / fwd,
+                    "forward_and_backward_over_forward": (ckf + bwd) / fwd,
+                    "backward_zone_updates_per_s": units / seconds,
+                    "gpu_launches_backward": 9 * steps + A.segments + 3}
+        A.close()
+        s.close()
+    return out
 
 
 def world_size(dist):

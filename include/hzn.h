@@ -195,6 +195,45 @@ int hz_ensemble_results(hz_ensemble* ens, double* h_t, long long* h_steps, long 
 int hz_ensemble_autotune(hz_ensemble* ens, const double* d_prim, double t_probe, double cfl,
                          int* h_threads, int* h_ctas_per_sm, float* h_ms);
 
+/* ---- Adjoint (reverse-mode gradient) of a fixed-step run -------------------------------
+ * The paper motivates the method by inverse problems on astrophysical sources (§1) but has no
+ * adjoint; these calls differentiate the discrete update of §2.2/§3.2 exactly.  A forward run
+ * of nsteps RK3 steps of fixed size dt from a primitive state P(0) stores checkpoints; the
+ * backward call takes dJ/dP(n) (and optionally dJ/dU(n)) for any scalar J of the final state
+ * and returns dJ/dP(0).  Every branch of the forward update (MC limiter case, HLLE wave-speed
+ * bound, discriminant clamp, atmosphere reset, pressure floor) is frozen at the forward state;
+ * the Newton recovery of §2.2 is differentiated by the implicit-function theorem
+ * (dP/dU = (dU/dP)^{-1} at the recovered state).  At a pressure-floor reset the Jacobian is
+ * taken at the floored state.
+ *
+ * Memory: sqrt(nsteps)-step checkpointing.  The forward pass stores (P, U) every ckpt_every
+ * steps (ckpt_every <= 0 picks ceil(sqrt(nsteps))); the backward pass recomputes one segment
+ * at a time with the forward kernels into a tape of its 3 ckpt_every + 1 substep states.
+ * FP64 only (HZ_ERR_UNSUPPORTED for HZ_MIXED); cleaning on or off; any metric, 1-3 axes.
+ * Layouts of the gradients are those of the primitive / conserved state (9 x N doubles). */
+typedef struct hz_adjoint hz_adjoint;
+/* Device bytes hz_adjoint_create needs. */
+int hz_adjoint_workspace_bytes(const hz_grid* grid, const hz_options* opts, int nsteps,
+                               int ckpt_every, size_t* bytes);
+/* Create an adjoint driver on a context whose metric is set (hz_set_metric).  It uses the
+ * context's stream and kernels; d_workspace: caller-owned, 256-byte aligned, at least
+ * hz_adjoint_workspace_bytes.  The context must outlive the driver. */
+int hz_adjoint_create(hz_adjoint** adj, hz_ctx* ctx, int nsteps, double dt, int ckpt_every,
+                      void* d_workspace, size_t bytes);
+int hz_adjoint_destroy(hz_adjoint* adj);
+/* Checkpoint interval and number of segments in use (host outputs, either may be null). */
+int hz_adjoint_checkpoint_interval(const hz_adjoint* adj, int* h_every, int* h_segments);
+/* Set the context's primitive state to d_prim_in, advance nsteps steps of size dt storing the
+ * checkpoints, and copy the final primitive state to d_prim_out (may be null).  The context
+ * holds the final state afterwards, as after hz_step.  Asynchronous. */
+int hz_adjoint_forward(hz_adjoint* adj, const double* d_prim_in, double* d_prim_out);
+/* Reverse sweep of the last hz_adjoint_forward: d_gprim_out = dJ/dP(n), d_gcons_out =
+ * dJ/dU(n) or null (zero); writes d_gprim_in = dJ/dP(0).  The context's primitive and
+ * conserved state are left as the forward pass left them; its statistics (time, steps,
+ * maximum speed) are those of the recomputation.  Asynchronous.  HZ_ERR_STATE before a
+ * forward pass. */
+int hz_adjoint_backward(hz_adjoint* adj, const double* d_gprim_out, const double* d_gcons_out,
+                        double* d_gprim_in);
 /* ---- Whole update without allocation --------------------------------------------------
  * The paper has no counterpart to this call; it is a convenience of this library.
  *

@@ -36,7 +36,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "hzn.h")]
+    return (_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) +
+            sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(INCLUDE, "hzn.h")])
 
 
 def up_to_date() -> bool:

@@ -11,6 +11,7 @@
 #include <new>
 
 #include "hzn.h"
+#include "hzn_ctx.h"
 #include "hzn_internal.h"
 
 using namespace hzn;
@@ -101,6 +102,10 @@ __global__ void k_reset_scalars(DevScalars* sc) {
 
 __global__ void k_reset_vmax(DevScalars* sc) { sc->vmax_bits = 0ull; }
 
+}  // namespace
+
+namespace hzn {
+
 int grid_blocks(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152 * 16) b = 152 * 16;
@@ -109,13 +114,6 @@ int grid_blocks(long long n, int threads) {
 }
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? HZ_OK : HZ_ERR_CUDA; }
-
-struct Layout {
-  size_t scal, met, u_bytes, p_bytes, total;
-  long long fs, ms;
-  int pitch, mpitch, mny;
-  long long plane, mplane;
-};
 
 Layout layout_of(const hz_grid* g, const hz_options* o) {
   Layout L;
@@ -158,29 +156,6 @@ int check_args(const hz_grid* g, const hz_options* o) {
   return HZ_OK;
 }
 
-}  // namespace
-
-// ----------------------------------------------------------------------------------------
-struct hz_ctx {
-  hz_grid g;
-  hz_options o;
-  cudaStream_t st;
-  KParams kp;
-  Variant v;
-  char* ws;
-  size_t wsbytes;
-  DevScalars* sc;
-  void* met;
-  double* U0;
-  double* U1;
-  void* P[2];
-  int cur;
-  int have_metric, have_prim;
-  int zchunks;
-};
-
-namespace {
-
 void launch_pack_in(hz_ctx* c, const double* src, void* dst) {
   const long long n = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
   const int zero_from = c->o.cleaning ? NF : 8;
@@ -199,17 +174,28 @@ void launch_pack_out(hz_ctx* c, const void* src, bool is_double, double* dst) {
     k_pack_out<float><<<grid_blocks(n * NF, 256), 256, 0, c->st>>>(c->kp, (const float*)src, dst, NF, zero_from);
 }
 
-int run_step(hz_ctx* c, int mode, double dt, double cfl, double t_end) {
-  if (!c->have_metric || !c->have_prim) return HZ_ERR_STATE;
+void launch_clock(hz_ctx* c, int mode, double dt, double cfl, double t_end) {
   k_clock<<<1, 1, 0, c->st>>>(c->sc, mode, dt, cfl, t_end);
-  const int a = c->cur, b = 1 - c->cur;
+}
+
+// The three substeps of one RK3 step with explicit primitive buffers Pin -> P1 -> P2 -> Pout
+// (Pin may equal P2, P1 may equal Pout); the conserved state lives in c->U0 / c->U1 and the
+// step size in the device clock.
+void launch_rk3(hz_ctx* c, const void* Pin, void* P1, void* P2, void* Pout) {
   // Shu-Osher RK3: U1 = U0 + dt L(U0); U2 = 3/4 U0 + 1/4 (U1 + dt L(U1)); U3 = 1/3 U0 + 2/3 (U2 + dt L(U2))
-  const StageArgs s1 = {c->P[a], c->P[b], c->U0, c->U0, c->U1, 0.0, 1.0, 0};
-  const StageArgs s2 = {c->P[b], c->P[a], c->U0, c->U1, c->U1, 0.75, 0.25, 0};
-  const StageArgs s3 = {c->P[a], c->P[b], c->U0, c->U1, c->U0, 1.0 / 3.0, 2.0 / 3.0, 1};
+  const StageArgs s1 = {Pin, P1, c->U0, c->U0, c->U1, 0.0, 1.0, 0};
+  const StageArgs s2 = {P1, P2, c->U0, c->U1, c->U1, 0.75, 0.25, 0};
+  const StageArgs s3 = {P2, Pout, c->U0, c->U1, c->U0, 1.0 / 3.0, 2.0 / 3.0, 1};
   launch_substep(c->v, c->kp, s1, c->met, c->sc, c->zchunks, c->st);
   launch_substep(c->v, c->kp, s2, c->met, c->sc, c->zchunks, c->st);
   launch_substep(c->v, c->kp, s3, c->met, c->sc, c->zchunks, c->st);
+}
+
+int run_step(hz_ctx* c, int mode, double dt, double cfl, double t_end) {
+  if (!c->have_metric || !c->have_prim) return HZ_ERR_STATE;
+  launch_clock(c, mode, dt, cfl, t_end);
+  const int a = c->cur, b = 1 - c->cur;
+  launch_rk3(c, c->P[a], c->P[b], c->P[a], c->P[b]);
   c->cur = b;
   return cuda_err(cudaGetLastError());
 }
@@ -287,7 +273,7 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   return cuda_err(cudaGetLastError());
 }
 
-}  // namespace
+}  // namespace hzn
 
 extern "C" {
 

@@ -475,3 +475,149 @@ class Ensemble:
 
     def results(self):
         return hz_ensemble_results(self.ens, len(self.n))
+
+
+# ------------------------------------------------------------------ adjoint of a fixed-step run
+ADJOINT_EXPORTED = (
+    "hz_adjoint_workspace_bytes", "hz_adjoint_create", "hz_adjoint_destroy",
+    "hz_adjoint_checkpoint_interval", "hz_adjoint_forward", "hz_adjoint_backward",
+)
+
+
+def _adj_lib():
+    L = lib()
+    if not getattr(L, "_adj_ready", False):
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        ip = P(ctypes.c_int)
+        L.hz_adjoint_workspace_bytes.argtypes = [P(hz_grid), P(hz_options), ctypes.c_int, ctypes.c_int,
+                                                 P(ctypes.c_size_t)]
+        L.hz_adjoint_create.argtypes = [P(vp), vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
+                                        ctypes.c_size_t]
+        L.hz_adjoint_destroy.argtypes = [vp]
+        L.hz_adjoint_checkpoint_interval.argtypes = [vp, ip, ip]
+        L.hz_adjoint_forward.argtypes = [vp, vp, vp]
+        L.hz_adjoint_backward.argtypes = [vp, vp, vp, vp]
+        for name in ADJOINT_EXPORTED:
+            getattr(L, name).restype = ctypes.c_int
+        L._adj_ready = True
+    return L
+
+
+def hz_adjoint_workspace_bytes(grid: hz_grid, opts: hz_options, nsteps: int, ckpt_every: int = 0) -> int:
+    n = ctypes.c_size_t(0)
+    _check(_adj_lib().hz_adjoint_workspace_bytes(ctypes.byref(grid), ctypes.byref(opts), int(nsteps),
+                                                 int(ckpt_every), ctypes.byref(n)),
+           "hz_adjoint_workspace_bytes")
+    return int(n.value)
+
+
+def hz_adjoint_create(ctx: int, nsteps: int, dt: float, ckpt_every: int, d_workspace: int, nbytes: int) -> int:
+    h = ctypes.c_void_p(0)
+    _check(_adj_lib().hz_adjoint_create(ctypes.byref(h), ctx, int(nsteps), float(dt), int(ckpt_every),
+                                        d_workspace, nbytes), "hz_adjoint_create")
+    return h.value
+
+
+def hz_adjoint_destroy(adj: int) -> None:
+    _check(_adj_lib().hz_adjoint_destroy(adj), "hz_adjoint_destroy")
+
+
+def hz_adjoint_checkpoint_interval(adj: int):
+    every, segs = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_adj_lib().hz_adjoint_checkpoint_interval(adj, ctypes.byref(every), ctypes.byref(segs)),
+           "hz_adjoint_checkpoint_interval")
+    return int(every.value), int(segs.value)
+
+
+def hz_adjoint_forward(adj: int, d_prim_in: int, d_prim_out: int) -> None:
+    _check(_adj_lib().hz_adjoint_forward(adj, d_prim_in, d_prim_out), "hz_adjoint_forward")
+
+
+def hz_adjoint_backward(adj: int, d_gprim_out: int, d_gcons_out: Optional[int], d_gprim_in: int) -> None:
+    _check(_adj_lib().hz_adjoint_backward(adj, d_gprim_out, d_gcons_out, d_gprim_in), "hz_adjoint_backward")
+
+
+class Adjoint:
+    """Reverse-mode gradient of ``nsteps`` fixed steps of size ``dt`` on a Solver's grid.
+
+    ``forward(prim0)`` runs the steps (storing sqrt(n) checkpoints) and returns the final
+    primitives; ``backward(gprim)`` returns dJ/dP(0) for dJ/dP(n) = gprim.  ``evolve(prim0)`` is
+    the same pair as a differentiable torch operation (torch.autograd.Function)."""
+
+    def __init__(self, solver: Solver, nsteps: int, dt: float, ckpt_every: int = 0):
+        t = solver.torch
+        self.torch = t
+        self.solver = solver
+        self.nsteps = int(nsteps)
+        self.dt = float(dt)
+        nbytes = hz_adjoint_workspace_bytes(solver.grid, solver.options, nsteps, ckpt_every)
+        self.workspace = t.empty(nbytes + 256, dtype=t.uint8, device=solver.device)
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.adj = hz_adjoint_create(solver.ctx, nsteps, dt, ckpt_every, base, nbytes)
+        self.checkpoint_every, self.segments = hz_adjoint_checkpoint_interval(self.adj)
+        self.generation = 0
+
+    def close(self):
+        if getattr(self, "adj", None):
+            hz_adjoint_destroy(self.adj)
+            self.adj = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, prim0):
+        s = self.solver
+        p = s._dev(prim0)
+        if tuple(p.shape) != s._shape():
+            raise ValueError(f"primitive shape {tuple(p.shape)} != {s._shape()}")
+        out = self.torch.empty(s._shape(), dtype=self.torch.float64, device=s.device)
+        hz_adjoint_forward(self.adj, p.data_ptr(), out.data_ptr())
+        self._keep_in = p
+        self.generation += 1
+        return out
+
+    def backward(self, gprim, gcons=None):
+        s = self.solver
+        g = s._dev(gprim)
+        gc = s._dev(gcons) if gcons is not None else None
+        out = self.torch.empty(s._shape(), dtype=self.torch.float64, device=s.device)
+        hz_adjoint_backward(self.adj, g.data_ptr(), gc.data_ptr() if gc is not None else None,
+                            out.data_ptr())
+        self._keep_g = (g, gc)
+        return out
+
+    def evolve(self, prim0):
+        return _evolve_function().apply(prim0, self)
+
+
+_EVOLVE_FN = None
+
+
+def _evolve_function():
+    """torch.autograd.Function over Adjoint.forward / Adjoint.backward (built on first use so
+    that importing this module does not import torch)."""
+    global _EVOLVE_FN
+    if _EVOLVE_FN is None:
+        import torch
+
+        class HorizonEvolve(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, prim0, adj):
+                out = adj.forward(prim0.detach())
+                ctx.adj = adj
+                ctx.generation = adj.generation
+                return out
+
+            @staticmethod
+            def backward(ctx, gout):
+                if ctx.adj.generation != ctx.generation:
+                    raise RuntimeError("the checkpoints of this forward pass were overwritten by a "
+                                       "later forward pass of the same Adjoint")
+                return ctx.adj.backward(gout.contiguous()), None
+
+        _EVOLVE_FN = HorizonEvolve
+    return _EVOLVE_FN

@@ -359,3 +359,142 @@ def with_periodic_metric(prob: Problem, met_fn) -> Problem:
     Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
     prob.metric = np.ascontiguousarray(met_fn(X, Y, Z))
     return prob
+
+
+# ------------------------------------------------------------------ gradient (adjoint) workloads
+# The 1-D inverse problem: the initial state of the magnetised shock tube is described by ten
+# left / right parameters and an additive density perturbation per cell; the loss is the L2
+# misfit of the final density against a target profile.  B^x is not a parameter: a jump in it
+# would violate the divergence constraint (§2.1).
+#
+# Base point.  On an exactly uniform state every limited slope sits on the kink of |x|, and in
+# the tails of the waves neighbouring cells differ by a few ulps, so the frozen-branch
+# derivative there depends on rounding: per-cell gradients of an untextured tube differ by
+# percents between two correct implementations (FMA contraction alone does it).  The base
+# point of the per-cell density parameters is therefore a seeded texture of relative size 1e-3,
+# and a fixed seeded texture of the same size is added to p, u~^i, B^y and B^z; B^x stays
+# uniform (its slopes are exactly zero and stay so).  Derivatives at this generic point agree
+# between implementations to round-off.
+TUBE_PARAM_NAMES = ("rho_L", "p_L", "vx_L", "By_L", "Bz_L", "rho_R", "p_R", "vx_R", "By_R", "Bz_R")
+TUBE_PARAMS_DEFAULT = np.array([1.0, 1.0, 0.0, 1.0, 0.0, 0.125, 0.1, 0.0, -1.0, 0.0])
+TUBE_BX = 0.5
+TUBE_TEXTURE = 1e-3
+
+
+def tube_texture(n: int, seed: int = 1104, amp: float = TUBE_TEXTURE) -> np.ndarray:
+    """(9, n): row 0 is the base value of the per-cell density perturbation (relative to the
+    side's density); rows 1-4, 6, 7 the fixed additive texture of p (relative to the side's
+    pressure), u~^x, u~^y, u~^z, B^y, B^z; rows 5 (B^x) and 8 (psi) are zero."""
+    rng = np.random.default_rng(seed)
+    left = (np.arange(n) + 0.5) / n < 0.5
+    t = np.zeros((9, n))
+    if amp == 0.0:
+        return t
+    t[0] = amp * np.where(left, TUBE_PARAMS_DEFAULT[0], TUBE_PARAMS_DEFAULT[5]) * rng.standard_normal(n)
+    t[1] = amp * np.where(left, TUBE_PARAMS_DEFAULT[1], TUBE_PARAMS_DEFAULT[6]) * rng.standard_normal(n)
+    for f in (2, 3, 4, 6, 7):
+        t[f] = amp * rng.standard_normal(n)
+    return t
+
+
+def tube_prim_from_params(theta, drho, n: int, xp=np, texture=None):
+    """Primitives (9, 1, 1, n) of the tube on [-0.5, 0.5] from the ten parameters, the per-cell
+    density perturbation drho (length n) and an optional fixed texture (rows 1-7 of
+    tube_texture are added; row 0 is the base value of drho, not added here).  ``xp`` is numpy
+    or torch (then the map is differentiable by autograd); u~^x = W v^x, W = 1/sqrt(1 - v^2)."""
+    if xp is np:
+        left = (np.arange(n) + 0.5) / n < 0.5
+        sel = lambda a, b: np.where(left, a, b)
+        zeros = np.zeros(n)
+        stack = np.stack
+        tex = texture
+    else:
+        left = (xp.arange(n, dtype=xp.float64, device=drho.device) + 0.5) / n < 0.5
+        sel = lambda a, b: xp.where(left, a, b)
+        zeros = xp.zeros(n, dtype=xp.float64, device=drho.device)
+        stack = xp.stack
+        tex = None if texture is None else xp.as_tensor(texture, dtype=xp.float64, device=drho.device)
+    rho = sel(theta[0], theta[5]) + drho
+    p = sel(theta[1], theta[6]) + zeros
+    v = sel(theta[2], theta[7]) + zeros
+    ut = v / xp.sqrt(1.0 - v * v)
+    by = sel(theta[3], theta[8]) + zeros
+    bz = sel(theta[4], theta[9]) + zeros
+    bx = zeros + TUBE_BX
+    uy, uz = zeros, zeros
+    if tex is not None:
+        p = p + tex[1]
+        ut = ut + tex[2]
+        uy = uy + tex[3]
+        uz = uz + tex[4]
+        by = by + tex[6]
+        bz = bz + tex[7]
+    prim = stack([rho, p, ut, uy, uz, bx, by, bz, zeros])
+    return prim.reshape(9, 1, 1, n)
+
+
+def adjoint_tube(n: int = 800, cfl: float = 0.4, steps: int = 1000, seed: int = 1104,
+                 texture: float = TUBE_TEXTURE) -> Problem:
+    """Gradient workload, 1-D: the tube of ``balsara1`` (Gamma = 2) at N cells at the textured
+    base point above, ``steps`` fixed steps of size fixed_dt = cfl * dx (a light-speed bound,
+    independent of the parameters)."""
+    P = shock_tube(n, BALSARA1_LEFT, BALSARA1_RIGHT, 2.0, 0.0, name="adjoint_tube", cfl=cfl)
+    tex = tube_texture(n, seed, texture)
+    P.prim = np.ascontiguousarray(tube_prim_from_params(TUBE_PARAMS_DEFAULT, tex[0], n, texture=tex))
+    P.steps = steps
+    P.t_end = steps * cfl * P.dx[0]
+    return P
+
+
+def fixed_dt(P: Problem) -> float:
+    """Fixed step of the gradient workloads: the light-speed bound of the unsplit update,
+    dt = cfl / sum over active axes of 1/dx_d (the Courant numbers of the axes add up; with
+    fast waves near c, dt = cfl * dx alone is linearly unstable in 2-D and the derivative of a
+    long run grows without bound even though the state looks fine)."""
+    return P.cfl / sum(1.0 / P.dx[d] for d in range(3) if P.n[d] > 1)
+
+
+def blast2d(n: int = 256, half_width: float = 6.0, r_in: float = 0.8, rho_in: float = 0.01,
+            p_in: float = 1.0, rho_out: float = 1e-4, p_out: float = 5e-4, bx: float = 0.1,
+            gamma: float = 4.0 / 3.0, cfl: float = 0.4, steps: int = 200) -> Problem:
+    """Gradient workload, 2-D: cylindrical magnetised blast wave on [-L, L]^2 (n^2 cells,
+    Minkowski, outflow): rho_in, p_in inside r < r_in, ambient rho_out, p_out outside, uniform
+    B^x, at rest; ``steps`` fixed steps of size fixed_dt (cfl * dx / 2)."""
+    dx = 2.0 * half_width / n
+    c = -half_width + (np.arange(n) + 0.5) * dx
+    y, x = np.meshgrid(c, c, indexing="ij")
+    inner = np.sqrt(x * x + y * y) < r_in
+    prim = np.zeros((9, 1, n, n))
+    prim[0, 0] = np.where(inner, rho_in, rho_out)
+    prim[1, 0] = np.where(inner, p_in, p_out)
+    prim[5, 0] = bx
+    nn = (n, n, 1)
+    return Problem(name="blast2d", n=nn, dx=(dx, dx, 1.0), x0=(-half_width, -half_width, 0.0),
+                   bc=(0, 0, 0), gamma=gamma, prim=prim, metric=minkowski_metric(nn),
+                   t_end=steps * 0.5 * cfl * dx, cfl=cfl, steps=steps)
+
+
+def blast2d_inner_mask(P: Problem, r_in: float = 0.8) -> np.ndarray:
+    """Cells of the blast wave's inner region (where the inner pressure parameter acts)."""
+    n = P.n[0]
+    c = P.x0[0] + (np.arange(n) + 0.5) * P.dx[0]
+    y, x = np.meshgrid(c, c, indexing="ij")
+    return (np.sqrt(x * x + y * y) < r_in)[None, :, :]
+
+
+def tube_param_directions(theta, n: int):
+    """d prim(0) / d theta_q for the ten tube parameters (analytic; du~/dv = W^3)."""
+    left = (np.arange(n) + 0.5) / n < 0.5
+    out = []
+    for q in range(10):
+        side = left if q < 5 else ~left
+        k = q % 5
+        d = np.zeros((9, 1, 1, n))
+        field = (0, 1, 2, 6, 7)[k]
+        val = 1.0
+        if k == 2:
+            v = theta[q]
+            val = (1.0 - v * v) ** -1.5
+        d[field, 0, 0, side] = val
+        out.append(d)
+    return out

@@ -24,7 +24,8 @@ def lib():
 
 
 def test_header_declares_binding_names():
-    assert set(declared_functions()) == set(hzn.EXPORTED) | set(hzn.ENSEMBLE_EXPORTED)
+    assert set(declared_functions()) == (set(hzn.EXPORTED) | set(hzn.ENSEMBLE_EXPORTED) |
+                                         set(hzn.ADJOINT_EXPORTED))
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -69,3 +70,23 @@ def test_workspace_bytes_and_argument_checks(lib):
                          None) == hzn.HZ_ERR_WORKSPACE
     assert lib.hz_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(o), ctypes.c_void_p(4096),
                          nb - 8, None) == hzn.HZ_ERR_WORKSPACE
+
+
+def test_adjoint_workspace_and_argument_checks(lib):
+    g = hzn.make_grid((800, 1, 1), (1.0 / 800, 1, 1), (0, 0, 0))
+    o = hzn.make_options(2.0)
+    nb = hzn.hz_adjoint_workspace_bytes(g, o, 1000, 0)
+    # 32 checkpoints of (P, U) + a tape of 3*32+1 states + 7 cell arrays + 2 face arrays
+    per = 9 * 832 * 8  # 800 cells padded to a field stride of 832
+    assert nb >= (32 * 2 + 97 + 7) * per
+    assert nb < (32 * 2 + 97 + 7 + 4) * per + 300 * 256
+    n = ctypes.c_size_t(0)
+    L = hzn._adj_lib()
+    mixed = hzn.make_options(2.0, precision=hzn.HZ_MIXED)
+    assert L.hz_adjoint_workspace_bytes(ctypes.byref(g), ctypes.byref(mixed), 10, 0,
+                                        ctypes.byref(n)) == hzn.HZ_ERR_UNSUPPORTED
+    assert L.hz_adjoint_workspace_bytes(ctypes.byref(g), ctypes.byref(o), 0, 0,
+                                        ctypes.byref(n)) == hzn.HZ_ERR_ARG
+    h = ctypes.c_void_p(0)
+    assert L.hz_adjoint_create(ctypes.byref(h), None, 10, 0.1, 0, None, 0) == hzn.HZ_ERR_ARG
+    assert L.hz_adjoint_backward(None, None, None, None) == hzn.HZ_ERR_ARG

@@ -1,0 +1,363 @@
+"""Adjoint (reverse-mode gradient) of the CUDA update against the FP64 oracle's complex-step
+derivative and against central finite differences.
+
+The adjoint differentiates the discrete update with every branch (MC case, HLLE bound, floor
+reset) frozen at the forward state, and the recovery by the implicit-function theorem; the
+oracle's complex step takes the same branches on the real part and carries the derivative
+through its own (different) recovery iteration.  The two are independent computations of the
+same derivative; the bar is 1e-6 relative (the benchmark statement's gradient tolerance), and
+they agree far closer.  Central differences of the GPU forward pass check the same numbers
+along directions in which the loss is differentiable (uniform rescaling of the tube's states;
+on a uniform state every limited slope sits on a kink of |x|)."""
+import numpy as np
+import pytest
+
+from parity import oracle_setup
+from paper_1102_5202_gb300 import hzn
+from paper_1102_5202_gb300 import workloads as W
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1102_5202_gb300 import build
+    build.build_library()
+    hzn.lib()
+
+
+def gpu_gradient(P, nsteps, dt, gfun, ckpt=0):
+    """(final primitives, dJ/dP(0)) with dJ/dP(n) = gfun(final primitives), all numpy."""
+    import torch
+
+    s = hzn.Solver.for_problem(P)
+    A = hzn.Adjoint(s, nsteps, dt, ckpt)
+    end = A.forward(P.prim)
+    g_end = torch.as_tensor(gfun(end.cpu().numpy()), dtype=torch.float64, device="cuda")
+    g0 = A.backward(g_end)
+    torch.cuda.synchronize()
+    out = end.cpu().numpy(), g0.cpu().numpy(), s.stats()
+    A.close()
+    s.close()
+    return out
+
+
+def cs_directional(P, nsteps, dt, direction, weights):
+    """Oracle complex-step derivative of J = sum(weights * P(n)) along direction."""
+    grid, opts = oracle_setup(P)
+    _, dend, _, _, nf = O.evolve_cs(grid, opts, P.metric, P.prim, direction, 1e-30, dt, nsteps)
+    return float((weights * dend).sum()), nf
+
+
+def _weights(P, seed, fields=range(8)):
+    rng = np.random.default_rng(seed)
+    w = np.zeros_like(P.prim)
+    for f in fields:
+        w[f] = rng.standard_normal(P.prim[f].shape)
+    return w
+
+
+def _check_directions(P, nsteps, dt, dirs, seed=1, fields=range(8), tol=TOL_GRAD):
+    w = _weights(P, seed, fields)
+    _, g0, st = gpu_gradient(P, nsteps, dt, lambda end: w)
+    worst = 0.0
+    for d in dirs:
+        ref, _ = cs_directional(P, nsteps, dt, d, w)
+        got = float((g0 * d).sum())
+        rel = abs(got - ref) / max(abs(ref), 1e-300)
+        worst = max(worst, rel)
+        assert rel <= tol, (got, ref, rel)
+    return worst, g0, st
+
+
+def test_tube_directions_against_complex_step():
+    """Textured tube (a generic point): per-cell and mixed directions.  The untextured tube:
+    directions uniform over each initial state, the only ones in which its loss is
+    differentiable."""
+    P = W.adjoint_tube(100, steps=30)
+    dt = 0.4 * P.dx[0]
+    n = P.n[0]
+    rng = np.random.default_rng(2)
+    d_left_p = np.zeros_like(P.prim)
+    d_left_p[1, ..., : n // 2] = 1.0
+    d_cell_rho = np.zeros_like(P.prim)
+    d_cell_rho[0] = rng.standard_normal(P.prim[0].shape) * 0.1
+    d_all = rng.standard_normal(P.prim.shape) * 0.1
+    d_all[5] = d_all[8] = 0.0
+    worst, _, _ = _check_directions(P, 30, dt, [d_left_p, d_cell_rho, d_all])
+    plain = W.balsara1(100)
+    d_right_rho = np.zeros_like(plain.prim)
+    d_right_rho[0, ..., n // 2:] = 1.0
+    worst_plain, _, _ = _check_directions(plain, 30, dt, [d_left_p, d_right_rho])
+    print(f"tube N=100, 30 steps: worst relative error of the directional derivative {worst:.2e} "
+          f"(textured), {worst_plain:.2e} (plain, uniform directions)")
+
+
+def test_tube_per_cell_density_gradient_elementwise():
+    """Every component dJ/d(rho_i(0)) of a density misfit, one complex-step run per cell."""
+    P = W.adjoint_tube(48, steps=15)
+    dt = 0.4 * P.dx[0]
+    rng = np.random.default_rng(9)
+    grid, opts = oracle_setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    ref_end = O.evolve(grid, opts, P.metric, P.prim, U, 1e30, 0.0, fixed_dt=dt, max_steps=15)[0]
+    target = ref_end[0] * (1.0 + 0.05 * rng.standard_normal(ref_end[0].shape))
+
+    def gfun(end):
+        g = np.zeros_like(end)
+        g[0] = 2.0 * (end[0] - target) * P.dx[0]
+        return g
+
+    _, g0, _ = gpu_gradient(P, 15, dt, gfun)
+    w = gfun(ref_end)
+    ref = np.zeros(P.n[0])
+    for i in range(P.n[0]):
+        d = np.zeros_like(P.prim)
+        d[0, 0, 0, i] = 1.0
+        ref[i], _ = cs_directional(P, 15, dt, d, w)
+    got = g0[0, 0, 0]
+    rel = np.abs(got - ref).sum() / np.abs(ref).sum()
+    assert rel <= TOL_GRAD, rel
+    print(f"tube N=48: per-cell density gradient, relative L1 error {rel:.2e}")
+
+
+def test_general_metric_cleaning_2d_periodic():
+    from test_gpu_parity import _general_metric
+
+    P = W.smooth_periodic((14, 10, 1), seed=5, amp=0.2, magnetised=True)
+    P = W.with_periodic_metric(P, _general_metric)
+    P.cleaning, P.ch, P.kappa = True, 0.6, 0.7
+    P.prim = P.prim.copy()
+    P.prim[8] = 0.01 * np.random.default_rng(4).standard_normal(P.prim[8].shape)
+    grid, opts = oracle_setup(P)
+    dt = 0.3 / O.max_speed(grid, opts, P.metric, P.prim)
+    rng = np.random.default_rng(8)
+    dirs = [rng.standard_normal(P.prim.shape) * 0.1 for _ in range(3)]
+    for d in dirs:
+        d[5:8] = 0.0  # the field stays divergence-free
+    worst, _, _ = _check_directions(P, 4, dt, dirs, fields=range(9))
+    print(f"2-D periodic, general metric, cleaning: worst relative error {worst:.2e}")
+
+
+def test_curved_3d_metric_outflow_cleaning():
+    """Metric source terms (the blob's curved static metric), outflow faces on three axes and
+    divergence cleaning: the blob raised onto a dense smooth background (no vacuum, so the
+    recovery stays well conditioned everywhere)."""
+    P = W.blob3d(16)
+    P.prim = P.prim.copy()
+    P.prim[0] += 0.05 * P.prim[0].max()
+    P.prim[1] += 0.05 * P.prim[1].max()
+    P.rho_atm = 0.0
+    P.prim[8] = 1e-3 * np.random.default_rng(6).standard_normal(P.prim[8].shape)
+    grid, opts = oracle_setup(P)
+    dt = 0.3 / O.max_speed(grid, opts, P.metric, P.prim)
+    rng = np.random.default_rng(12)
+    dirs = []
+    for _ in range(2):
+        d = np.zeros_like(P.prim)
+        for f in (0, 1, 2, 3, 4, 8):
+            d[f] = rng.standard_normal(P.prim[f].shape) * (np.abs(P.prim[f]).max() + 1e-3) * 0.1
+        dirs.append(d)
+    worst, _, st = _check_directions(P, 3, dt, dirs, fields=range(9))
+    assert st.c2p_failures == 0
+    print(f"curved 16^3, 3 steps, cleaning: worst relative error {worst:.2e}")
+
+
+def test_atmosphere_resets():
+    """A tube expanding into vacuum: the right state is below the atmosphere threshold, so its
+    cells (and those the rarefaction empties) are reset to the atmosphere every substep; the
+    reset is frozen (only B and psi of a reset cell depend on its conserved state)."""
+    left = dict(rho=1.0, p=1.0, Bx=0.3, By=0.6)
+    right = dict(rho=1e-9, p=1e-9, Bx=0.3, By=0.2)
+    P = W.shock_tube(80, left, right, 5.0 / 3.0, 0.0, name="vacuum_tube")
+    P.rho_floor, P.rho_atm, P.p_floor, P.atm_K = 1e-9, 1e-7, 1e-12, 0.0
+    rng = np.random.default_rng(21)
+    P.prim = P.prim.copy()
+    n = P.n[0]
+    for f in (0, 1):
+        P.prim[f, ..., : n // 2] *= 1.0 + 1e-3 * rng.standard_normal(n // 2)
+    for f in (2, 3, 6):
+        P.prim[f, ..., : n // 2] += 1e-3 * rng.standard_normal(n // 2)
+    dt = 0.4 * P.dx[0]
+    dirs = []
+    for _ in range(2):
+        d = np.zeros_like(P.prim)
+        for f in (0, 1, 2, 3, 6):
+            d[f, ..., : n // 2] = 0.1 * rng.standard_normal(n // 2)
+        dirs.append(d)
+    worst, _, st = _check_directions(P, 20, dt, dirs, fields=range(8))
+    assert st.c2p_failures == 0
+    print(f"vacuum tube, 20 steps: worst relative error {worst:.2e}")
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    P = W.adjoint_tube(64, steps=12)
+    dt = 0.4 * P.dx[0]
+    w = _weights(P, 3)
+    grads = [gpu_gradient(P, 12, dt, lambda end: w, ckpt=k)[1] for k in (1, 5, 0, 12)]
+    for g in grads[1:]:
+        assert np.array_equal(g, grads[0])
+
+
+def test_autograd_function_with_tube_parameters():
+    """Loss of the ten tube parameters through torch autograd (parameter map in torch, the run
+    through the C-ABI adjoint) against central differences of the GPU forward pass."""
+    import torch
+
+    n, steps = 200, 100
+    P = W.adjoint_tube(n, steps=steps)
+    dt = W.fixed_dt(P)
+    s = hzn.Solver.for_problem(P)
+    A = hzn.Adjoint(s, steps, dt)
+    theta0 = torch.tensor(W.TUBE_PARAMS_DEFAULT, dtype=torch.float64, device="cuda")
+    tex = W.tube_texture(n)
+    drho = torch.as_tensor(tex[0], dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(1104)
+    with torch.no_grad():
+        end = A.forward(W.tube_prim_from_params(theta0, drho, n, xp=torch, texture=tex))
+    target = end[0] * torch.as_tensor(1.0 + 0.05 * rng.standard_normal(end[0].shape), device="cuda")
+
+    def loss(theta, dr):
+        prim = W.tube_prim_from_params(theta, dr, n, xp=torch, texture=tex)
+        out = A.evolve(prim)
+        return ((out[0] - target) ** 2).sum() * P.dx[0]
+
+    th = theta0.clone().requires_grad_(True)
+    dr = drho.clone().requires_grad_(True)
+    J = loss(th, dr)
+    J.backward()
+    g = th.grad.cpu().numpy()
+    # central differences cross limiter branch switches for any finite step (an error that
+    # shrinks with the step) and lose digits to round-off for a tiny one: take the best of a
+    # few steps
+    errs = []
+    with torch.no_grad():
+        for hrel in (1e-6, 1e-7, 1e-8):
+            fd = np.zeros(10)
+            for q in range(10):
+                h = hrel * max(abs(W.TUBE_PARAMS_DEFAULT[q]), 1.0)
+                e = torch.zeros(10, dtype=torch.float64, device="cuda")
+                e[q] = h
+                fd[q] = float(loss(theta0 + e, drho) - loss(theta0 - e, drho)) / (2 * h)
+            errs.append(np.abs(g - fd).max() / np.abs(g).max())
+    err = min(errs)
+    assert err <= 1e-5, errs
+    assert dr.grad is not None and torch.isfinite(dr.grad).all()
+    print(f"tube N=200, 100 steps: parameter gradient vs central differences, max error / max |g| "
+          f"{err:.1e} (steps 1e-6, 1e-7, 1e-8: {', '.join('%.1e' % x for x in errs)})")
+
+
+def test_config_tube_full_size_against_complex_step_and_fd():
+    """The 1-D gradient workload at full size: N=800, 1000 fixed steps.  dJ/dtheta for the ten
+    parameters and dJ/d(rho_i) for a sample of cells against the oracle's complex step (one
+    run per component), and the parameters against central differences of the GPU forward."""
+    import torch
+
+    P = W.adjoint_tube(800)
+    n, steps, dt = P.n[0], P.steps, W.fixed_dt(P)
+    rng = np.random.default_rng(1104)
+    grid, opts = oracle_setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    ref_end = O.evolve(grid, opts, P.metric, P.prim, U, 1e30, 0.0, fixed_dt=dt, max_steps=steps)[0]
+    target = ref_end[0] * (1.0 + 0.05 * rng.standard_normal(ref_end[0].shape))
+
+    def gfun(end):
+        g = np.zeros_like(end)
+        g[0] = 2.0 * (end[0] - target) * P.dx[0]
+        return g
+
+    end, g0, st = gpu_gradient(P, steps, dt, gfun)
+    assert st.c2p_failures == 0
+    w = gfun(ref_end)
+    # parameter directions d prim / d theta_q of the tube map
+    dirs = W.tube_param_directions(W.TUBE_PARAMS_DEFAULT, n)
+    g_theta = np.array([(g0 * d).sum() for d in dirs])
+    ref_theta = np.array([cs_directional(P, steps, dt, d, w)[0] for d in dirs])
+    rel = np.abs(g_theta - ref_theta) / np.abs(ref_theta).max()
+    assert rel.max() <= TOL_GRAD, (g_theta, ref_theta)
+    cells = rng.choice(n, size=6, replace=False)
+    ref_cells = []
+    for i in cells:
+        d = np.zeros_like(P.prim)
+        d[0, 0, 0, i] = 1.0
+        ref_cells.append(cs_directional(P, steps, dt, d, w)[0])
+    ref_cells = np.array(ref_cells)
+    got_cells = g0[0, 0, 0, cells]
+    rel_c = np.abs(got_cells - ref_cells) / np.abs(g0[0]).max()
+    assert rel_c.max() <= TOL_GRAD, (got_cells, ref_cells)
+    # central differences of the GPU forward pass along the parameter directions
+    s = hzn.Solver.for_problem(P)
+    tgt = torch.as_tensor(target, device="cuda")
+
+    def J(prim):
+        s.set_primitives(prim)
+        for _ in range(steps):
+            s.step(dt)
+        r = s.primitives()[0]
+        return float(((r - tgt) ** 2).sum() * P.dx[0])
+
+    # Central differences cross limiter branch switches for any finite step.  After 1000 steps
+    # the switches are so dense along every parameter direction that the difference quotient
+    # settles only for steps near 1e-10, where round-off of J leaves about 3e-5: the complex
+    # step above is the exact reference, this is the independent cross-check (best of three
+    # steps, bound 1e-4 of the largest component).
+    rel_fd = np.full(10, np.inf)
+    for eps in (1e-8, 1e-9, 1e-10):
+        for k, d in enumerate(dirs):
+            fd = (J(P.prim + eps * d) - J(P.prim - eps * d)) / (2 * eps)
+            rel_fd[k] = min(rel_fd[k], abs(g_theta[k] - fd) / np.abs(ref_theta).max())
+    assert rel_fd.max() <= 1e-4, rel_fd
+    print(f"tube N=800, 1000 steps: parameter gradient vs complex step max rel {rel.max():.1e}; "
+          f"per-cell density (6 cells) {rel_c.max():.1e}; vs central differences (best step) "
+          f"{rel_fd.max():.1e}")
+
+
+def test_blast2d_inner_pressure():
+    """2-D cylindrical blast wave: dJ/dp_in (the inner pressure, one scalar acting on every cell
+    of the inner region) against the oracle's complex step at 128^2 x 100 steps and against
+    central differences of the GPU forward pass at the full 256^2 x 200 steps."""
+    def run(P, check_cs):
+        steps, dt = P.steps, W.fixed_dt(P)
+        mask = W.blast2d_inner_mask(P)
+        d = np.zeros_like(P.prim)
+        d[1] = mask * 1.0
+
+        def gfun(end):
+            g = np.zeros_like(end)
+            g[0] = 2.0 * end[0] * P.dx[0] * P.dx[1]
+            return g
+
+        end, g0, st = gpu_gradient(P, steps, dt, gfun)
+        got = float((g0 * d).sum())
+        out = {"adjoint": got, "fails": st.c2p_failures}
+        if check_cs:
+            grid, opts = oracle_setup(P)
+            pr, dend, _, _, _ = O.evolve_cs(grid, opts, P.metric, P.prim, d, 1e-30, dt, steps)
+            out["cs"] = float((gfun(pr) * dend).sum())
+        else:
+            s = hzn.Solver.for_problem(P)
+
+            def J(prim):
+                s.set_primitives(prim)
+                for _ in range(steps):
+                    s.step(dt)
+                r = s.primitives()[0]
+                return float((r * r).sum() * P.dx[0] * P.dx[1])
+
+            out["fd"] = {eps: (J(P.prim + eps * d) - J(P.prim - eps * d)) / (2 * eps)
+                         for eps in (1e-5, 1e-6, 1e-7, 1e-8)}
+        return out
+
+    small = run(W.blast2d(128, steps=100), True)
+    assert small["fails"] == 0
+    assert abs(small["adjoint"] - small["cs"]) <= TOL_GRAD * abs(small["cs"]), small
+    full = run(W.blast2d(256), False)
+    assert full["fails"] == 0
+    errs = {eps: abs(full["adjoint"] - v) / abs(full["adjoint"]) for eps, v in full["fd"].items()}
+    assert min(errs.values()) <= 1e-5, (full, errs)
+    print(f"blast 128^2 x 100: adjoint {small['adjoint']:.12e} complex step {small['cs']:.12e}; "
+          f"blast 256^2 x 200: adjoint {full['adjoint']:.10e}, central differences relative error "
+          + ", ".join(f"{e:.0e}: {v:.1e}" for e, v in errs.items()))
