@@ -44,6 +44,7 @@ class Opts(ctypes.Structure):
         ("atm_K", ctypes.c_double),
         ("c2p_maxit", ctypes.c_int),
         ("rho_atm", ctypes.c_double),
+        ("recon", ctypes.c_int),
     ]
 
 
@@ -92,6 +93,7 @@ def lib():
             L.hzo_evolve_cs.argtypes = [gp, op, dp, dp, dp, ctypes.c_double, ctypes.c_long, dp, dp, dp,
                                         dp]
             L.hzo_evolve_cs.restype = ctypes.c_long
+            L.hzo_reconstruct_1d.argtypes = [ctypes.c_int, ctypes.c_long, dp, dp, dp]
             L.hzo_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -106,11 +108,14 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+RECON_MC, RECON_PPM = 0, 1
+
+
 def make_opts(gamma: float, cleaning: bool = False, ch: float = 0.0, kappa: float = 0.0,
               rho_floor: float = 1e-12, p_floor: float = 1e-14, atm_K: float = 0.0,
-              c2p_maxit: int = 200, rho_atm: float = 0.0) -> Opts:
+              c2p_maxit: int = 200, rho_atm: float = 0.0, recon: int = RECON_MC) -> Opts:
     return Opts(float(gamma), int(bool(cleaning)), float(ch), float(kappa), float(rho_floor),
-                float(p_floor), float(atm_K), int(c2p_maxit), float(rho_atm))
+                float(p_floor), float(atm_K), int(c2p_maxit), float(rho_atm), int(recon))
 
 
 def make_grid(n, dx, bc) -> Grid:
@@ -266,3 +271,13 @@ def evolve_cs(grid: Grid, opts: Opts, met, prim, dprim, h: float, dt: float, nst
     nf = lib().hzo_evolve_cs(ctypes.byref(grid), ctypes.byref(opts), _dp(met), _dp(pre), _dp(pim),
                              float(dt), int(nsteps), _dp(ore), _dp(oim), _dp(cre), _dp(cim))
     return ore, oim / float(h), cre, cim / float(h), int(nf)
+
+
+def reconstruct_1d(recon: int, q):
+    """(left, right) face states of a 1-D array at the faces between cells c-1 and c, for
+    c = 3 .. n-3 (entries outside that range are NaN)."""
+    q = _f64(q)
+    n = q.shape[0]
+    left, right = np.full(n, np.nan), np.full(n, np.nan)
+    lib().hzo_reconstruct_1d(int(recon), n, _dp(q), _dp(left), _dp(right))
+    return left, right

@@ -89,6 +89,7 @@ typedef struct {
   double atm_K;      // atmosphere pressure = atm_K rho_floor^gamma if > 0, else p_floor
   int c2p_maxit;     // iteration cap of the recovery
   double rho_atm;    // cells with D / sqrt(gamma) below rho_atm are set to the atmosphere (0: off)
+  int recon;         // 0: TVD with the MC limiter; 1: PPM (§3.2)
 } hzo_opts;
 
 }  // extern "C"
@@ -281,6 +282,56 @@ static R mc_slope(const R& dm, const R& dp) {
   if (re(dm) * re(dp) <= 0.0) return R(0.0);
   R a = minv(minv(2.0 * absv(dm), 2.0 * absv(dp)), 0.5 * absv(dm + dp));
   return re(dp) > 0.0 ? a : -a;
+}
+
+// PPM (§3.2, the piecewise parabolic method of Colella and Woodward as used by Marti and Muller):
+// the interface value between cells u and u+1 interpolates the parabola through the
+// neighbouring cell values, written with the MC-limited slopes sigma,
+//   a_{u+1/2} = (q_u + q_{u+1}) / 2 - (sigma_{u+1} - sigma_u) / 6,
+// then each cell's pair (aL, aR) is made monotone: a cell at a local extremum becomes flat
+// (aL = aR = q); otherwise an edge value that would put the parabola's extremum inside the
+// cell is moved to 3 q - 2 (other edge).  No contact steepening, no flattening (the paper
+// names the method only).
+template <class R>
+static R ppm_edge(const R& qa, const R& qb, const R& sa, const R& sb) {
+  return 0.5 * (qa + qb) - (sb - sa) / 6.0;
+}
+
+template <class R>
+static void ppm_monotone(R& aL, const R& q, R& aR) {
+  if (re(aR - q) * re(q - aL) <= 0.0) {
+    aL = q;
+    aR = q;
+    return;
+  }
+  const R d = aR - aL;
+  const R m6 = 6.0 * (q - 0.5 * (aL + aR));
+  if (re(d) * re(m6) > re(d) * re(d)) aL = 3.0 * q - 2.0 * aR;
+  else if (-re(d) * re(d) > re(d) * re(m6)) aR = 3.0 * q - 2.0 * aL;
+}
+
+// Left and right states at the face between cells c-1 and c from the six cells c-3 .. c+2
+// (q[0] .. q[5]): MC uses q[1] .. q[4], PPM all six.
+template <class R>
+static void reconstruct(int recon, const R q[6], R* left, R* right) {
+  if (recon == 0) {
+    R sigL = mc_slope(q[2] - q[1], q[3] - q[2]);  // slope in cell c-1
+    R sigR = mc_slope(q[3] - q[2], q[4] - q[3]);  // slope in cell c
+    *left = q[2] + 0.5 * sigL;
+    *right = q[3] - 0.5 * sigR;
+    return;
+  }
+  R sig[4];  // MC slopes of cells c-2 .. c+1
+  for (int u = 0; u < 4; ++u) sig[u] = mc_slope(q[u + 1] - q[u], q[u + 2] - q[u + 1]);
+  R e0 = ppm_edge(q[1], q[2], sig[0], sig[1]);  // between c-2 and c-1
+  R e1 = ppm_edge(q[2], q[3], sig[1], sig[2]);  // between c-1 and c
+  R e2 = ppm_edge(q[3], q[4], sig[2], sig[3]);  // between c and c+1
+  R aL1 = e0, aR1 = e1;                         // cell c-1
+  ppm_monotone(aL1, q[2], aR1);
+  R aL2 = e1, aR2 = e2;                         // cell c
+  ppm_monotone(aL2, q[3], aR2);
+  *left = aR1;
+  *right = aL2;
 }
 
 // HLLE flux of one component (§2.2: needs only the two fluxes and the two wave-speed bounds).
@@ -496,10 +547,10 @@ static int recover_cell(const Geom<R>& G, R U[NCONS], const R Pguess[NPRIM], con
 
 // ----------------------------------------------------------------------------------------
 // Grid storage.  Grid functions are plain arrays, x fastest, one array per field.
-// Primitive arrays are copied into a ghost-padded work array (width NG = 2 on active axes);
+// Primitive arrays are copied into a ghost-padded work array (width NG = 3 on active axes);
 // the metric comes with one ghost layer on active axes.
 // ----------------------------------------------------------------------------------------
-constexpr int NG = 2;
+constexpr int NG = 3;
 
 struct Mesh {
   hzo_grid g;
@@ -590,11 +641,8 @@ static void rhs(const Mesh& M, const hzo_opts& o, const double* met, const R* pr
         auto at = [&](int s) {
           return Pp[(size_t)f * npd + M.pcell(i + s * e[0], j + s * e[1], k + s * e[2])];
         };
-        R pm2 = at(-2), pm1 = at(-1), p0 = at(0), pp1 = at(1);
-        R sigL = mc_slope(pm1 - pm2, p0 - pm1);  // slope in cell c-1
-        R sigR = mc_slope(p0 - pm1, pp1 - p0);   // slope in cell c
-        PL[f] = pm1 + 0.5 * sigL;
-        PR[f] = p0 - 0.5 * sigR;
+        R q[6] = {at(-3), at(-2), at(-1), at(0), at(1), at(2)};
+        reconstruct(o.recon, q, &PL[f], &PR[f]);
       }
       R mA[NMET], mB[NMET], mf[NMET];
       load_metric(M, met, M.mcell(i - e[0], j - e[1], k - e[2]), mA);
@@ -938,6 +986,13 @@ long hzo_evolve_cs(const hzo_grid* g, const hzo_opts* o, const double* met, cons
     if (cons_im) cons_im[q] = U[q].imag();
   }
   return fails;
+}
+
+// Left / right face states of a 1-D array q[0 .. n-1] (n >= 6) at the faces between cells c-1 and
+// c for c = 3 .. n-3 (the faces whose six-cell stencil lies inside the array): left[c], right[c];
+// the other entries are left untouched.  recon: 0 MC, 1 PPM.
+void hzo_reconstruct_1d(int recon, long n, const double* q, double* left, double* right) {
+  for (long c = 3; c + 2 < n; ++c) reconstruct(recon, q + c - 3, &left[c], &right[c]);
 }
 
 int hzo_num_threads(void) {

@@ -55,6 +55,8 @@ class Problem:
     p_floor: float = 1e-14
     atm_K: float = 0.0
     steps: int = 0                          # fixed step count of the benchmark problems
+    recon: int = 0                          # reconstruction: 0 MC, 1 PPM (§3.2)
+    c2p: int = 0                            # GPU recovery scheme: 0 2D Newton, 1 1D Newton (§3.2)
 
     @property
     def ncell(self) -> int:

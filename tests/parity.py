@@ -16,7 +16,7 @@ TOL_END = 1e-8
 def oracle_setup(P):
     grid = O.make_grid(P.n, P.dx, P.bc)
     opts = O.make_opts(P.gamma, cleaning=P.cleaning, ch=P.ch, kappa=P.kappa, rho_floor=P.rho_floor,
-                       p_floor=P.p_floor, atm_K=P.atm_K, rho_atm=P.rho_atm)
+                       p_floor=P.p_floor, atm_K=P.atm_K, rho_atm=P.rho_atm, recon=P.recon)
     return grid, opts
 
 
