@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--ensemble-tubes", type=int, default=512)
     ap.add_argument("--n-mixed", type=int, default=384, help="cells per axis of the mixed line")
     return ap.parse_args()
@@ -237,6 +238,10 @@ def run_gpu(args, rank, world, local):
     if not args.no_adjoint:
         adjoint = run_adjoint(args, dist, local)
 
+    variants = None
+    if not args.no_variants:
+        variants = run_variants(args, dist, local, base_zu_per_s=value)
+
     line = None
     if rank == 0:
         cpu = None
@@ -257,6 +262,7 @@ def run_gpu(args, rank, world, local):
             "mixed": mixed,
             "ensemble": ensemble,
             "adjoint": adjoint,
+            "variants": variants,
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "c2p_failures": int(st.c2p_failures),
@@ -366,6 +372,48 @@ def run_adjoint(args, dist, local, reps: int = 3):
                     "gpu_launches_backward": 9 * steps + A.segments + 3}
         A.close()
         s.close()
+    return out
+
+
+def run_variants(args, dist, local, base_zu_per_s: float, steps: int = 5, warmup: int = 2):
+    """The scheme variants of §3.2 on the FP64 blob at the benchmark size, each timed like the
+    main line (CUDA events on the solver's stream, CFL 0.5 steps): PPM reconstruction, the 1D
+    recovery scheme, and the toroidal-field initial data of §5.2."""
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+    from paper_1102_5202_gb300 import workloads as W
+
+    out = {}
+    for name in ("ppm", "c2p_1d", "toroidal"):
+        P = W.blob3d(args.n, field="toroidal" if name == "toroidal" else "poloidal")
+        if name == "ppm":
+            P.recon = hzn.HZ_RECON_PPM
+        if name == "c2p_1d":
+            P.c2p = hzn.HZ_C2P_1D
+        s = hzn.Solver.for_problem(P)
+        for _ in range(warmup):
+            s.step_cfl(0.5, 1e30)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s.stream):
+            a.record(s.stream)
+            for _ in range(steps):
+                s.step_cfl(0.5, 1e30)
+            b.record(s.stream)
+        b.synchronize()
+        sec = a.elapsed_time(b) * 1e-3
+        st = s.stats()
+        units, seconds = aggregate(float(P.ncell) * steps, sec, dist, device=torch.device("cuda", local))
+        out[name] = {"workload": f"{P.name}_fp64" + ("_ppm" if name == "ppm" else "") +
+                     ("_c2p1d" if name == "c2p_1d" else ""), "value": units / seconds, "unit": UNIT,
+                     "steps": steps, "ms_per_step": seconds / steps * 1e3,
+                     "relative_to_mc_2d_poloidal": units / seconds / base_zu_per_s,
+                     "c2p_failures": int(st.c2p_failures), "gpu_launches": 4 * steps}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
     return out
 
 

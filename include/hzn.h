@@ -51,6 +51,8 @@ enum {
 
 enum { HZ_BC_OUTFLOW = 0, HZ_BC_PERIODIC = 1 };
 enum { HZ_FP64 = 0, HZ_MIXED = 1 };
+enum { HZ_RECON_MC = 0, HZ_RECON_PPM = 1 };
+enum { HZ_C2P_2D = 0, HZ_C2P_1D = 1 };
 
 typedef struct hz_ctx hz_ctx; /* opaque; host-side bookkeeping, owned by the library */
 
@@ -80,6 +82,13 @@ typedef struct {
   double atm_K;     /* atmosphere pressure = atm_K rho_floor^gamma when > 0, else p_floor */
   int c2p_maxit;    /* Newton iteration cap of the recovery (1 .. 200)                    */
   double c2p_tol;   /* Newton stop: |dZ| <= c2p_tol Z (1e-15 .. 1e-6)                     */
+  int recon;        /* HZ_RECON_MC: TVD with the MC limiter.  HZ_RECON_PPM: the piecewise
+                       parabolic method (§3.2; interface parabola from MC-limited slopes, then
+                       the monotonicity constraints; no steepening or flattening); needs at
+                       least 3 cells on every active axis (HZ_ERR_UNSUPPORTED otherwise)       */
+  int c2p;          /* HZ_C2P_2D: Newton in (Z, v^2), FP32 then FP64 (§3.2 "2D").  HZ_C2P_1D:
+                       Newton in Z alone with v^2 eliminated, kept in its bracket by bisection
+                       (§3.2 "1D").  Both return the same root to round-off                    */
 } hz_options;
 
 typedef struct {
@@ -147,8 +156,9 @@ int hz_version(void);
  * time in one persistent launch.  Each tube has its own cell count n[t] >= 2, cell width dx[t]
  * and adiabatic index gamma[t], Minkowski spacetime, outflow boundaries, and its own CFL time
  * step; the scheme is that of the grid path (MC, HLLE, RK3, Newton recovery; §2.2, §3.2) in
- * FP64 without divergence cleaning (opts->precision = HZ_FP64, opts->cleaning = 0; the floors,
- * rho_atm, atm_K and the recovery options of hz_options apply).  A persistent grid of thread
+ * FP64 without divergence cleaning (opts->precision = HZ_FP64, opts->cleaning = 0,
+ * opts->recon = HZ_RECON_MC, opts->c2p = HZ_C2P_2D; the floors, rho_atm, atm_K and the recovery
+ * options of hz_options apply).  A persistent grid of thread
  * blocks takes tubes from a work queue, most cells first; one block owns a tube for all its
  * steps, so no grid-wide synchronisation is needed.
  *
@@ -209,7 +219,8 @@ int hz_ensemble_autotune(hz_ensemble* ens, const double* d_prim, double t_probe,
  * Memory: sqrt(nsteps)-step checkpointing.  The forward pass stores (P, U) every ckpt_every
  * steps (ckpt_every <= 0 picks ceil(sqrt(nsteps))); the backward pass recomputes one segment
  * at a time with the forward kernels into a tape of its 3 ckpt_every + 1 substep states.
- * FP64 only (HZ_ERR_UNSUPPORTED for HZ_MIXED); cleaning on or off; any metric, 1-3 axes.
+ * FP64 with MC reconstruction only (HZ_ERR_UNSUPPORTED for HZ_MIXED or HZ_RECON_PPM); cleaning
+ * on or off; either recovery scheme; any metric, 1-3 axes.
  * Layouts of the gradients are those of the primitive / conserved state (9 x N doubles). */
 typedef struct hz_adjoint hz_adjoint;
 /* Device bytes hz_adjoint_create needs. */

@@ -176,7 +176,7 @@ int hz_adjoint_workspace_bytes(const hz_grid* grid, const hz_options* opts, int 
   if (!bytes || nsteps < 1) return HZ_ERR_ARG;
   const int e = check_args(grid, opts);
   if (e != HZ_OK) return e;
-  if (opts->precision != HZ_FP64) return HZ_ERR_UNSUPPORTED;
+  if (opts->precision != HZ_FP64 || opts->recon != HZ_RECON_MC) return HZ_ERR_UNSUPPORTED;
   *bytes = adj_layout(grid, opts, nsteps, ckpt_every).total;
   return HZ_OK;
 }
@@ -186,7 +186,7 @@ int hz_adjoint_create(hz_adjoint** adj, hz_ctx* ctx, int nsteps, double dt, int 
   if (!adj) return HZ_ERR_ARG;
   *adj = nullptr;
   if (!ctx || nsteps < 1 || !(dt > 0.0)) return HZ_ERR_ARG;
-  if (ctx->o.precision != HZ_FP64) return HZ_ERR_UNSUPPORTED;
+  if (ctx->o.precision != HZ_FP64 || ctx->o.recon != HZ_RECON_MC) return HZ_ERR_UNSUPPORTED;
   if (!ctx->have_metric) return HZ_ERR_STATE;
   const AdjLayout A = adj_layout(&ctx->g, &ctx->o, nsteps, ckpt_every);
   if (!d_workspace || ((uintptr_t)d_workspace & 255u) != 0 || bytes < A.total) return HZ_ERR_WORKSPACE;

@@ -153,6 +153,12 @@ int check_args(const hz_grid* g, const hz_options* o) {
   if (!(o->rho_atm >= 0.0)) return HZ_ERR_ARG;
   if (o->c2p_maxit < 1 || o->c2p_maxit > 200) return HZ_ERR_ARG;
   if (!(o->c2p_tol >= 1e-15) || o->c2p_tol > 1e-6) return HZ_ERR_ARG;
+  if (o->recon != HZ_RECON_MC && o->recon != HZ_RECON_PPM) return HZ_ERR_ARG;
+  if (o->c2p != HZ_C2P_2D && o->c2p != HZ_C2P_1D) return HZ_ERR_ARG;
+  // PPM reads three cells on each side: an active axis needs at least three cells
+  if (o->recon == HZ_RECON_PPM)
+    for (int d = 0; d < 3; ++d)
+      if (g->n[d] > 1 && g->n[d] < 3) return HZ_ERR_UNSUPPORTED;
   return HZ_OK;
 }
 
@@ -222,6 +228,7 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   c->v.dims = grid->n[2] > 1 ? 3 : (grid->n[1] > 1 ? 2 : 1);
   c->v.clean = opts->cleaning;
   c->v.mixed = opts->precision == HZ_MIXED;
+  c->v.recon = opts->recon;
   c->v.diag = 0;
 
   KParams& kp = c->kp;
@@ -255,6 +262,7 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   kp.p_atm = patm < opts->p_floor ? opts->p_floor : patm;
   kp.c2p_maxit = opts->c2p_maxit;
   kp.c2p_tol = opts->c2p_tol;
+  kp.c2p_1d = opts->c2p == HZ_C2P_1D;
   // z chunks: enough blocks for several waves on 152 SMs
   int tx, ty;
   tile_of(c->v.dims, &tx, &ty);

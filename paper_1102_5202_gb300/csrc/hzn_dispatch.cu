@@ -1,4 +1,4 @@
-// Dispatch of the kernel launchers on dimensionality and precision.
+// Dispatch of the kernel launchers on dimensionality, precision and reconstruction.
 #include "hzn_kernels.cuh"
 
 namespace hzn {
@@ -15,9 +15,31 @@ HZN_DECLARE(32, 1)
 HZN_DECLARE(32, 2)
 HZN_DECLARE(32, 3)
 #undef HZN_DECLARE
+#define HZN_DECLARE_PPM(P, D)                                                                      \
+  void launch_substep_k##P##p_##D##d(const Variant&, const KParams&, const StageArgs&, const void*, \
+                                     DevScalars*, int, cudaStream_t);
+HZN_DECLARE_PPM(64, 1)
+HZN_DECLARE_PPM(64, 2)
+HZN_DECLARE_PPM(64, 3)
+HZN_DECLARE_PPM(32, 1)
+HZN_DECLARE_PPM(32, 2)
+HZN_DECLARE_PPM(32, 3)
+#undef HZN_DECLARE_PPM
 
 void launch_substep(const Variant& v, const KParams& kp, const StageArgs& sa, const void* M,
                     DevScalars* sc, int zchunks, cudaStream_t st) {
+  if (v.recon) {
+    if (v.mixed) {
+      if (v.dims == 1) launch_substep_k32p_1d(v, kp, sa, M, sc, zchunks, st);
+      else if (v.dims == 2) launch_substep_k32p_2d(v, kp, sa, M, sc, zchunks, st);
+      else launch_substep_k32p_3d(v, kp, sa, M, sc, zchunks, st);
+    } else {
+      if (v.dims == 1) launch_substep_k64p_1d(v, kp, sa, M, sc, zchunks, st);
+      else if (v.dims == 2) launch_substep_k64p_2d(v, kp, sa, M, sc, zchunks, st);
+      else launch_substep_k64p_3d(v, kp, sa, M, sc, zchunks, st);
+    }
+    return;
+  }
   if (v.mixed) {
     if (v.dims == 1) launch_substep_k32_1d(v, kp, sa, M, sc, zchunks, st);
     else if (v.dims == 2) launch_substep_k32_2d(v, kp, sa, M, sc, zchunks, st);

@@ -428,7 +428,8 @@ int hz_ensemble_create(hz_ensemble** out, int ntubes, const int* h_n, const doub
     if (h_n[t] < 2 || h_n[t] > (1 << 24)) return HZ_ERR_ARG;
     if (!(h_dx[t] > 0.0) || !(h_gamma[t] > 1.0) || h_gamma[t] > 3.0) return HZ_ERR_ARG;
   }
-  if (opts->precision != HZ_FP64 || opts->cleaning) return HZ_ERR_UNSUPPORTED;
+  if (opts->precision != HZ_FP64 || opts->cleaning || opts->recon != HZ_RECON_MC || opts->c2p != HZ_C2P_2D)
+    return HZ_ERR_UNSUPPORTED;
   if (!(opts->rho_floor > 0.0) || !(opts->p_floor > 0.0) || opts->c2p_maxit < 1 ||
       opts->c2p_maxit > 200 || !(opts->c2p_tol >= 1e-15) || opts->c2p_tol > 1e-6)
     return HZ_ERR_ARG;

@@ -32,6 +32,7 @@ struct KParams {
   double rho_floor, rho_atm, p_floor, p_atm;
   int c2p_maxit;
   double c2p_tol;
+  int c2p_1d;            // 1: the 1D recovery scheme (Newton in z, v^2 eliminated)
   int zlen;              // cells of z per block
 };
 
@@ -52,6 +53,7 @@ struct Variant {
   int clean;   // divergence cleaning
   int diag;    // zero shift and diagonal gamma everywhere
   int mixed;   // FP32 storage of P and metric, FP32 faces/sources
+  int recon;   // 0 MC, 1 PPM
 };
 
 // Launchers, one per (precision, dims) translation unit; dispatch in hzn_dispatch.cu.

@@ -6,7 +6,7 @@ namespace hzn {
 
 void launch_substep_k32_3d(const Variant& v, const KParams& kp, const StageArgs& sa, const void* M,
                         DevScalars* sc, int zchunks, cudaStream_t st) {
-  launch_substep_t<true, true, true>(v, kp, sa, M, sc, zchunks, st);
+  launch_substep_t<true, true, true, 0>(v, kp, sa, M, sc, zchunks, st);
 }
 
 void launch_max_speed_k32_3d(const Variant& v, const KParams& kp, const void* P, const void* M,

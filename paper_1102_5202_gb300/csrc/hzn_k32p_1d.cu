@@ -1,0 +1,12 @@
+// Instantiations of the mixed-precision kernels with PPM reconstruction for 1-D grids (a unit of
+// its own so that the build runs the heavy instantiations in parallel).
+#include "hzn_kernels.cuh"
+
+namespace hzn {
+
+void launch_substep_k32p_1d(const Variant& v, const KParams& kp, const StageArgs& sa, const void* M,
+                            DevScalars* sc, int zchunks, cudaStream_t st) {
+  launch_substep_t<false, false, true, 1>(v, kp, sa, M, sc, zchunks, st);
+}
+
+}  // namespace hzn

@@ -6,7 +6,7 @@ namespace hzn {
 
 void launch_substep_k64_1d(const Variant& v, const KParams& kp, const StageArgs& sa, const void* M,
                         DevScalars* sc, int zchunks, cudaStream_t st) {
-  launch_substep_t<false, false, false>(v, kp, sa, M, sc, zchunks, st);
+  launch_substep_t<false, false, false, 0>(v, kp, sa, M, sc, zchunks, st);
 }
 
 void launch_max_speed_k64_1d(const Variant& v, const KParams& kp, const void* P, const void* M,

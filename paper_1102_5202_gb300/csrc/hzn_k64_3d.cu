@@ -6,7 +6,7 @@ namespace hzn {
 
 void launch_substep_k64_3d(const Variant& v, const KParams& kp, const StageArgs& sa, const void* M,
                         DevScalars* sc, int zchunks, cudaStream_t st) {
-  launch_substep_t<true, true, false>(v, kp, sa, M, sc, zchunks, st);
+  launch_substep_t<true, true, false, 0>(v, kp, sa, M, sc, zchunks, st);
 }
 
 void launch_max_speed_k64_3d(const Variant& v, const KParams& kp, const void* P, const void* M,

@@ -80,29 +80,36 @@ __device__ __forceinline__ void load_metric(const KParams& kp, const S* __restri
 
 // HLLE flux of the face at i - 1/2 along D of cell (i, j, k) (the face between cells i-1 and
 // i along D), written to out[f * ostride].
-template <int D, bool CLEAN, bool DIAG, typename R, typename S>
+// RECON 0: TVD with the MC limiter (stencil c-2 .. c+1); 1: PPM (stencil c-3 .. c+2).
+template <int D, bool CLEAN, bool DIAG, int RECON, typename R, typename S>
 __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict__ P,
                                           const S* __restrict__ M, int i, int j, int k, R* out,
                                           int ostride) {
   constexpr int NV = CLEAN ? 9 : 8;
-  long long off[4];  // stencil cells s = -2 .. 1 along D
+  constexpr int NS = RECON ? 6 : 4;
+  long long off[NS];  // stencil cells s = -NS/2 .. NS/2 - 1 along D
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
+  for (int s = 0; s < NS; ++s) {
     int ii = i, jj = j, kk = k;
-    if (D == 0) ii = bc_index(i + s - 2, kp.nx, kp.bcx);
-    if (D == 1) jj = bc_index(j + s - 2, kp.ny, kp.bcy);
-    if (D == 2) kk = bc_index(k + s - 2, kp.nz, kp.bcz);
+    if (D == 0) ii = bc_index(i + s - NS / 2, kp.nx, kp.bcx);
+    if (D == 1) jj = bc_index(j + s - NS / 2, kp.ny, kp.bcy);
+    if (D == 2) kk = bc_index(k + s - NS / 2, kp.nz, kp.bcz);
     off[s] = (long long)kk * kp.plane + (long long)jj * kp.pitch + ii;
   }
   R PL[9], PR[9];
 #pragma unroll
   for (int f = 0; f < NV; ++f) {
     const S* pf = P + f * kp.fs;
-    const R a = (R)__ldg(pf + off[0]), b = (R)__ldg(pf + off[1]);
-    const R cc = (R)__ldg(pf + off[2]), d = (R)__ldg(pf + off[3]);
-    const R d0 = b - a, d1 = cc - b, d2 = d - cc;
-    PL[f] = b + mc_half_slope(d0, d1);
-    PR[f] = cc - mc_half_slope(d1, d2);
+    if constexpr (RECON == 0) {
+      const R a = (R)__ldg(pf + off[0]), b = (R)__ldg(pf + off[1]);
+      const R cc = (R)__ldg(pf + off[2]), d = (R)__ldg(pf + off[3]);
+      const R d0 = b - a, d1 = cc - b, d2 = d - cc;
+      PL[f] = b + mc_half_slope(d0, d1);
+      PR[f] = cc - mc_half_slope(d1, d2);
+    } else {
+      ppm_face<R>((R)__ldg(pf + off[0]), (R)__ldg(pf + off[1]), (R)__ldg(pf + off[2]),
+                  (R)__ldg(pf + off[3]), (R)__ldg(pf + off[4]), (R)__ldg(pf + off[5]), PL[f], PR[f]);
+    }
   }
   if (!CLEAN) PL[8] = PR[8] = R(0);
   // face metric: mean of the two adjacent centre values
@@ -309,7 +316,7 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
   // recovered but set to the atmosphere state (the decision uses the conserved state only)
   const bool atm = U[U_D] < kp.rho_atm * G.sqrtg;
   C2PResult r = {1, 0};
-  if (!atm) r = con2prim<CLEAN, DIAG, ONE_FINISH>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_tol, P);
+  if (!atm) r = con2prim<CLEAN, DIAG, ONE_FINISH>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_tol, P, kp.c2p_1d);
   iters = r.iters;
   bool reset = false;
   if (atm || !r.ok || P[P_RHO] < kp.rho_floor) {
@@ -333,7 +340,7 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
   return r.ok ? 0 : 1;
 }
 
-template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED>
+template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED, int RECON>
 __global__ void __launch_bounds__(TX * TY, MIXED ? 3 : 2)
 k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* __restrict__ M,
           DevScalars* sc) {
@@ -360,28 +367,28 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   double vloc = 0.0;
   int nfail = 0, maxit = 0;
 
-  if (ZA && own) face_flux<2, CLEAN, DIAG>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX);
+  if (ZA && own) face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX);
 
   for (int k = kz0; k < kz1; ++k) {
     // ---- faces of plane k: each face of the tile once
-    if (i <= kp.nx && j < kp.ny) face_flux<0, CLEAN, DIAG>(kp, P, M, i, j, k, &fx[0][ty][tx], TY * (TX + 1));
-    if (YA && i < kp.nx && j <= kp.ny) face_flux<1, CLEAN, DIAG>(kp, P, M, i, j, k, &fy[0][ty][tx], (TY + 1) * TX);
-    if (ZA && own) face_flux<2, CLEAN, DIAG>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
+    if (i <= kp.nx && j < kp.ny) face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, i, j, k, &fx[0][ty][tx], TY * (TX + 1));
+    if (YA && i < kp.nx && j <= kp.ny) face_flux<1, CLEAN, DIAG, RECON>(kp, P, M, i, j, k, &fy[0][ty][tx], (TY + 1) * TX);
+    if (ZA && own) face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
     if (YA) {
       // top row of y-faces of the tile: warp 0; right column of x-faces: warp 1
       if (threadIdx.x < TX) {
         const int ii = i0 + threadIdx.x, jj = j0 + TY;
         if (ii < kp.nx && jj <= kp.ny)
-          face_flux<1, CLEAN, DIAG>(kp, P, M, ii, jj, k, &fy[0][TY][threadIdx.x], (TY + 1) * TX);
+          face_flux<1, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fy[0][TY][threadIdx.x], (TY + 1) * TX);
       } else if (threadIdx.x >= 32 && threadIdx.x < 32 + TY) {
         const int jj = j0 + (threadIdx.x - 32), ii = i0 + TX;
         if (ii <= kp.nx && jj < kp.ny)
-          face_flux<0, CLEAN, DIAG>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x - 32][TX], TY * (TX + 1));
+          face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x - 32][TX], TY * (TX + 1));
       }
     } else if (threadIdx.x < TY) {
       const int jj = j0 + threadIdx.x, ii = i0 + TX;
       if (ii <= kp.nx && jj < kp.ny)
-        face_flux<0, CLEAN, DIAG>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x][TX], TY * (TX + 1));
+        face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x][TX], TY * (TX + 1));
     }
     __syncthreads();
 
@@ -523,7 +530,7 @@ inline int grid_blocks(long long n, int threads) {
 }
 
 // Launchers for one (precision, dimensionality); dispatch on cleaning and metric class.
-template <bool YA, bool ZA, bool MIXED>
+template <bool YA, bool ZA, bool MIXED, int RECON>
 void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, const void* Mv,
                       DevScalars* sc, int zchunks, cudaStream_t st) {
   constexpr int TX = (!YA && !ZA) ? 128 : 32;
@@ -532,11 +539,11 @@ void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, 
   const S* M = (const S*)Mv;
   dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, zchunks);
   if (v.clean) {
-    if (v.diag) k_substep<TX, TY, YA, ZA, true, true, MIXED><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
-    else k_substep<TX, TY, YA, ZA, true, false, MIXED><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    if (v.diag) k_substep<TX, TY, YA, ZA, true, true, MIXED, RECON><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    else k_substep<TX, TY, YA, ZA, true, false, MIXED, RECON><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
   } else {
-    if (v.diag) k_substep<TX, TY, YA, ZA, false, true, MIXED><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
-    else k_substep<TX, TY, YA, ZA, false, false, MIXED><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    if (v.diag) k_substep<TX, TY, YA, ZA, false, true, MIXED, RECON><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    else k_substep<TX, TY, YA, ZA, false, false, MIXED, RECON><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
   }
 }
 

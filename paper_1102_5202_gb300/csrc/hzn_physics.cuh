@@ -296,6 +296,49 @@ __device__ __forceinline__ float mc_half_slope(float dm, float dp) {
   return dm * dp > 0.f ? s : 0.f;
 }
 
+// PPM (§3.2; the piecewise parabolic method of Colella and Woodward as used by Marti and
+// Muller).  Interface value between cells a and b from their values and MC half slopes:
+//   e = (qa + qb)/2 - (sigma_b - sigma_a)/6 = (qa + qb)/2 - (hb - ha)/3,
+// which is the interface value of the parabola through the neighbouring cells.
+template <typename R>
+__device__ __forceinline__ R ppm_edge(R qa, R qb, R ha, R hb) {
+  return R(0.5) * (qa + qb) - (hb - ha) * (R(1) / R(3));
+}
+
+// Monotonicity constraints of one cell's parabola (edge values aL, aR, cell value q): a cell at
+// a local extremum becomes flat; an edge that puts the parabola's extremum inside the cell is
+// moved to 3q - 2 (other edge), which places the extremum on the opposite edge.
+template <typename R>
+__device__ __forceinline__ void ppm_limit(R& aL, R q, R& aR) {
+  if ((aR - q) * (q - aL) <= R(0)) {
+    aL = q;
+    aR = q;
+    return;
+  }
+  const R d = aR - aL;
+  const R m6 = R(6) * (q - R(0.5) * (aL + aR));
+  if (d * m6 > d * d) aL = R(3) * q - R(2) * aR;
+  else if (-(d * d) > d * m6) aR = R(3) * q - R(2) * aL;
+}
+
+// Left / right states at the face between cells c-1 and c from the cells c-3 .. c+2.
+template <typename R>
+__device__ __forceinline__ void ppm_face(R q0, R q1, R q2, R q3, R q4, R q5, R& left, R& right) {
+  const R h0 = mc_half_slope(q1 - q0, q2 - q1);  // cell c-2
+  const R h1 = mc_half_slope(q2 - q1, q3 - q2);  // cell c-1
+  const R h2 = mc_half_slope(q3 - q2, q4 - q3);  // cell c
+  const R h3 = mc_half_slope(q4 - q3, q5 - q4);  // cell c+1
+  const R e0 = ppm_edge(q1, q2, h0, h1);
+  R e1 = ppm_edge(q2, q3, h1, h2);
+  const R e2 = ppm_edge(q3, q4, h2, h3);
+  R aL1 = e0, aR1 = e1;  // cell c-1
+  ppm_limit(aL1, q2, aR1);
+  R aL2 = e1, aR2 = e2;  // cell c
+  ppm_limit(aL2, q3, aR2);
+  left = aR1;
+  right = aL2;
+}
+
 // ------------------------------------------------------------------------------------------
 // Recovery of the primitive state from the conserved one (§2.2: Newton-Raphson, §3.2: the 2D
 // scheme).  With normal-observer quantities D = rho W, S_i, E, Bn^i, and the unknowns
@@ -420,10 +463,13 @@ __device__ __forceinline__ void c2p_apply(R& z, R& v2, NewtonStep<R> st) {
 // previous primitive state (initial guess).  maxit caps the FP64 iterations.  ONE_FINISH:
 // when the FP32 stage has settled, apply a single FP64 Newton correction (quadratic
 // convergence takes the 1e-7 FP32 error to ~1e-14, ample when the result is stored in FP32).
+//
+// one_d: the 1D scheme instead (§3.2 names a 1D and a 2D recovery): Newton in z alone with v^2
+// eliminated, from the previous state's z, kept in its bracket by bisection (c2p_bracketed).
 template <bool CLEAN, bool DIAG, bool ONE_FINISH = false>
 __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const double U[9],
                                               const double Pg[9], const Consts<double>& c,
-                                              int maxit, double tol, double P[9]) {
+                                              int maxit, double tol, double P[9], int one_d = 0) {
   const double isg = 1.0 / G.sqrtg;
   const double Dd = U[U_D] * isg;
   const double Sx = U[U_TX] * isg, Sy = U[U_TY] * isg, Sz = U[U_TZ] * isg;
@@ -478,9 +524,14 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
     v2 = uu / (1.0 + uu);
     if (!(z > 0.0) || !(z < 1e30)) z = q.e;
   }
-  // FP32 stage
   bool settled = false;
-  {
+  bool done = false;
+  if (one_d) {
+    if (!c2p_bracketed(q, z, z, v2, res.iters)) return res;
+    done = true;
+  }
+  // FP32 stage
+  if (!done) {
     float zf = (float)z, vf = (float)v2;
     const float ef = (float)q.e, sf = (float)q.s, qf = (float)q.q, bf = (float)q.b, gf = (float)g1;
     for (int it = 0; it < 30; ++it) {
@@ -500,8 +551,7 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
     }
   }
   // FP64 stage
-  bool done = false;
-  if (ONE_FINISH && settled) {
+  if (!done && ONE_FINISH && settled) {
     const NewtonStep<double> st = c2p_newton<double>(z, v2, q.e, q.s, q.q, q.b, g1);
     c2p_apply(z, v2, st);
     ++res.iters;

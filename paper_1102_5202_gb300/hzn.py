@@ -25,6 +25,8 @@ HZ_ERR_TOO_LARGE = -6
 HZ_NOALLOC_SCRATCH_BYTES = 16 << 20
 HZ_BC_OUTFLOW, HZ_BC_PERIODIC = 0, 1
 HZ_FP64, HZ_MIXED = 0, 1
+HZ_RECON_MC, HZ_RECON_PPM = 0, 1
+HZ_C2P_2D, HZ_C2P_1D = 0, 1
 
 EXPORTED = (
     "hz_workspace_bytes", "hz_create", "hz_destroy", "hz_set_metric", "hz_set_primitives",
@@ -50,6 +52,8 @@ class hz_options(ctypes.Structure):
         ("atm_K", ctypes.c_double),
         ("c2p_maxit", ctypes.c_int),
         ("c2p_tol", ctypes.c_double),
+        ("recon", ctypes.c_int),
+        ("c2p", ctypes.c_int),
     ]
 
 
@@ -202,10 +206,10 @@ def make_grid(n, dx, bc) -> hz_grid:
 def make_options(gamma: float, precision: int = HZ_FP64, cleaning: bool = False, ch: float = 0.0,
                  kappa: float = 0.0, rho_floor: float = 1e-12, rho_atm: float = 0.0,
                  p_floor: float = 1e-14, atm_K: float = 0.0, c2p_maxit: int = 50,
-                 c2p_tol: float = 1e-12) -> hz_options:
+                 c2p_tol: float = 1e-12, recon: int = HZ_RECON_MC, c2p: int = HZ_C2P_2D) -> hz_options:
     return hz_options(float(gamma), int(precision), int(bool(cleaning)), float(ch), float(kappa),
                       float(rho_floor), float(rho_atm), float(p_floor), float(atm_K), int(c2p_maxit),
-                      float(c2p_tol))
+                      float(c2p_tol), int(recon), int(c2p))
 
 
 class Solver:
@@ -232,8 +236,8 @@ class Solver:
                     **kw):
         opts = make_options(prob.gamma, precision=precision, cleaning=prob.cleaning, ch=prob.ch,
                             kappa=prob.kappa, rho_floor=prob.rho_floor, rho_atm=prob.rho_atm,
-                            p_floor=prob.p_floor,
-                            atm_K=prob.atm_K, c2p_maxit=c2p_maxit, c2p_tol=c2p_tol)
+                            p_floor=prob.p_floor, atm_K=prob.atm_K, c2p_maxit=c2p_maxit,
+                            c2p_tol=c2p_tol, recon=prob.recon, c2p=prob.c2p)
         s = cls(prob.n, prob.dx, prob.bc, opts, **kw)
         s.set_metric(prob.metric)
         s.set_primitives(prob.prim)

@@ -184,14 +184,35 @@ def blob_metric_fields(x, y, z):
     return alp, psi4
 
 
+# Gauss per code unit of field strength (G = c = M_sun = 1, Heaviside-Lorentz, magnetic
+# pressure b^2/2): b^2/2 = B_G^2 / (8 pi) / e_unit with e_unit = (M_sun / L^3) c^2 and
+# L = G M_sun / c^2, so B_code = B_G / sqrt(4 pi e_unit).
+GAUSS_PER_CODE_UNIT = 8.352e19
+TOROIDAL_B_GAUSS = 2.6e15      # largest field strength of the toroidal model (§5.2)
+TOROIDAL_VARPI0 = 3.0
+TOROIDAL_H = 1.0
+
+
+def toroidal_profile(X, Y, Z, varpi0: float = TOROIDAL_VARPI0, H: float = TOROIDAL_H):
+    """Field strength profile (varpi/varpi0)^2 exp(-varpi^2/varpi0^2) exp(-z^2/(2 H^2)) of the
+    toroidal model of §5.2.  The paper prints the last factor as exp(-z/2H), which is not even
+    in z; it is read as exp(-z^2/(2 H^2)).  The profile peaks at varpi = varpi0, z = 0 with
+    the value 1/e."""
+    w2 = (X * X + Y * Y) / (varpi0 * varpi0)
+    return w2 * np.exp(-w2) * np.exp(-Z * Z / (2.0 * H * H))
+
+
 def blob3d(n: int = 192, seed: int = 1102, half_width: float = 20.0, kappa: float = 1.0,
-           ch: float = 0.5, cleaning: bool = True, steps: int = 100) -> Problem:
+           ch: float = 0.5, cleaning: bool = True, steps: int = 100, field: str = "poloidal") -> Problem:
     """3-D rotating blob in a fixed curved spacetime (G = c = M_sun = 1).
 
     rho = rho_c (max(1 - (r/8)^2, 0) + 1e-10)(1 + 0.01 xi), xi ~ U[-1, 1] per cell (seeded);
-    p = K rho_unperturbed^Gamma; coordinate velocity Omega (-y, x, 0) inside r < 8;
-    poloidal B from A_phi = A_b max(p - 0.04 p_max, 0) varpi^2, with A_b scaled so that the
-    largest Eulerian magnetic pressure is 1e-3 of the largest gas pressure.
+    p = K rho_unperturbed^Gamma; coordinate velocity Omega (-y, x, 0) inside r < 8.
+    field = "poloidal": B from A_phi = A_b max(p - 0.04 p_max, 0) varpi^2, with A_b scaled so
+    that the largest Eulerian magnetic pressure is 1e-3 of the largest gas pressure.
+    field = "toroidal": the toroidal model of §5.2, Eulerian field B_n = B0 toroidal_profile e_phi
+    (unit vector of the spatial metric), B0 = e * 2.6e15 G so that the largest field strength is
+    2.6e15 G; B^z = 0 and sqrt(gamma) B^i is divergence-free (an axisymmetric toroidal field).
     """
     nn = (n, n, n)
     dx = 2.0 * half_width / n
@@ -239,15 +260,32 @@ def blob3d(n: int = 192, seed: int = 1102, half_width: float = 20.0, kappa: floa
     # flow toroidal, so Bn.v = 0 and b^2 = Bn^2 / W^2.
     b2_unit = psi4_c * alp_c ** 2 * (Bx * Bx + By * By + Bz * Bz) / (W * W)
     Ab = math.sqrt(1e-3 * float(p.max()) / max(float((0.5 * b2_unit).max()), 1e-300))
+    Bx, By, Bz = Ab * Bx, Ab * By, Ab * Bz
+    if field == "toroidal":
+        # Eulerian field alpha B^i = f e_phi^i with e_phi^i = (-y, x, 0) / (varpi psi^2), so that
+        # gamma_ij (alpha B^i)(alpha B^j) = f^2
+        B0 = math.e * TOROIDAL_B_GAUSS / GAUSS_PER_CODE_UNIT
+        varpi = np.sqrt(X * X + Y * Y)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            ex = np.where(varpi > 0, -Y / varpi, 0.0)
+            ey = np.where(varpi > 0, X / varpi, 0.0)
+        f = B0 * toroidal_profile(X, Y, Z)
+        psi2 = np.sqrt(psi4_c)
+        Bx = f * ex / (psi2 * alp_c)
+        By = f * ey / (psi2 * alp_c)
+        Bz = np.zeros_like(Bx)
+    elif field != "poloidal":
+        raise ValueError(f"unknown field {field!r}")
     prim = np.zeros((9,) + rho.shape)
     prim[0] = rho
     prim[1] = p
     prim[2] = W * vx
     prim[3] = W * vy
-    prim[5] = Ab * Bx
-    prim[6] = Ab * By
-    prim[7] = Ab * Bz
-    return Problem(name=f"blob3d_{n}", n=nn, dx=(dx,) * 3, x0=x0, bc=(0, 0, 0),
+    prim[5] = Bx
+    prim[6] = By
+    prim[7] = Bz
+    return Problem(name=f"blob3d_{n}" + ("" if field == "poloidal" else f"_{field}"), n=nn,
+                   dx=(dx,) * 3, x0=x0, bc=(0, 0, 0),
                    gamma=BLOB_GAMMA, prim=np.ascontiguousarray(prim), metric=met,
                    t_end=0.0, cfl=0.5, cleaning=cleaning, ch=ch, kappa=kappa,
                    rho_floor=BLOB_ATM * BLOB_RHOC, rho_atm=10.0 * BLOB_ATM * BLOB_RHOC,
