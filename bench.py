@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--adjoint-reps", type=int, default=3, help="timed repetitions of the adjoint leg")
+    ap.add_argument("--mixed-error", action="store_true",
+                    help="also run 100 FP64 steps at the mixed size and state the mixed error (about a minute)")
     ap.add_argument("--ensemble-tubes", type=int, default=512)
     ap.add_argument("--n-mixed", type=int, default=384, help="cells per axis of the mixed line")
     return ap.parse_args()
@@ -236,7 +239,7 @@ def run_gpu(args, rank, world, local):
 
     adjoint = None
     if not args.no_adjoint:
-        adjoint = run_adjoint(args, dist, local)
+        adjoint = run_adjoint(args, dist, local, reps=args.adjoint_reps)
 
     variants = None
     if not args.no_variants:
@@ -307,7 +310,9 @@ def run_mixed(args, dist, local, hbm_peak):
     fl = MIXED_FP64_FLOPS_PER_CELL_SUBSTEP * P.ncell / substep_s / 1e12
     del s
     torch.cuda.empty_cache()
+    err = mixed_error(P) if args.mixed_error else None
     return {"value": value, "unit": UNIT, "workload": f"blob3d_{args.n_mixed}^3_mixed_cleaning",
+            "error_vs_fp64_gpu_100_steps": err,
             "cells": P.ncell, "ms_per_step": seconds / args.steps * 1e3, "dtype": "f32/f64",
             "roofline": {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": fl / FP64_PEAK_TFLOPS,
@@ -318,6 +323,40 @@ def run_mixed(args, dist, local, hbm_peak):
                              "unit": "GB/s", "frac": ach / hbm_peak,
                              "roofline_zu_per_s": hbm_peak * 1e9 / HBM_BYTES_PER_ZU_MIXED},
             "c2p_failures": int(st.c2p_failures), "gpu_launches": 4 * args.steps}
+
+
+def mixed_error(P, steps: int = 100):
+    """Relative L1 per field of the mixed run against the FP64 GPU run of the same blob after
+    `steps` CFL steps (the FP64 run's time steps replayed), whole grid and star bulk."""
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+
+    s = hzn.Solver.for_problem(P)
+    dts = []
+    for _ in range(steps):
+        s.step_cfl(0.5, 1e30)
+        dts.append(s.stats().dt)
+    a = s.primitives().cpu().numpy()
+    del s
+    torch.cuda.empty_cache()
+    s = hzn.Solver.for_problem(P, precision=hzn.HZ_MIXED)
+    for dt in dts:
+        s.step(dt)
+    b = s.primitives().cpu().numpy()
+    fails = int(s.stats().c2p_failures)
+    del s
+    torch.cuda.empty_cache()
+
+    def rel(x, y):
+        den = np.array([np.abs(y[g, ...]).sum() if len(g) == 1 else
+                        np.sqrt((y[list(g)] ** 2).sum(axis=0)).sum() for g in
+                        ((0,), (1,), (2, 3, 4), (2, 3, 4), (2, 3, 4), (5, 6, 7), (5, 6, 7), (5, 6, 7), (8,))])
+        return [float(np.abs(x[f] - y[f]).sum() / max(den[f], 1e-300)) for f in range(9)]
+
+    star = a[0] > 0.1 * a[0].max()
+    return {"fields": ["rho", "p", "utx", "uty", "utz", "Bx", "By", "Bz", "psi"], "steps": steps,
+            "whole_grid": rel(b, a), "star_bulk": rel(b[:, star], a[:, star]), "mixed_c2p_failures": fails}
 
 
 def run_adjoint(args, dist, local, reps: int = 3):

@@ -81,7 +81,9 @@ typedef struct {
   double p_floor;   /* pressure floor                                                    */
   double atm_K;     /* atmosphere pressure = atm_K rho_floor^gamma when > 0, else p_floor */
   int c2p_maxit;    /* Newton iteration cap of the recovery (1 .. 200)                    */
-  double c2p_tol;   /* Newton stop: |dZ| <= c2p_tol Z (1e-15 .. 1e-6)                     */
+  double c2p_tol;   /* recovery accuracy (1e-15 .. 1e-6): the FP64 Newton iteration stops
+                       after a step |dZ| <= 0.01 sqrt(c2p_tol) Z (quadratic convergence then
+                       leaves an error below c2p_tol)                                         */
   int recon;        /* HZ_RECON_MC: TVD with the MC limiter.  HZ_RECON_PPM: the piecewise
                        parabolic method (§3.2; interface parabola from MC-limited slopes, then
                        the monotonicity constraints; no steepening or flattening); needs at
@@ -260,7 +262,7 @@ int hz_adjoint_backward(hz_adjoint* adj, const double* d_gprim_out, const double
  * Its scratch (the workspace hz_create would take) is one static device array of
  * HZ_NOALLOC_SCRATCH_BYTES (16 MiB) inside libhzn.so; every GPU that loads the library holds
  * it until the process exits.  A grid whose hz_workspace_bytes exceeds that size is rejected
- * with HZ_ERR_TOO_LARGE (for example 32^3 cells fit, 64^3 do not).
+ * with HZ_ERR_TOO_LARGE (for example 24^3 cells with cleaning fit, 32^3 do not).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before any
  *     stream capture.

@@ -106,6 +106,11 @@ namespace {
 
 inline void* tape_slot(hz_adjoint* a, int s) { return a->tape + (size_t)s * a->A.p_bytes; }
 
+// Threads per block of the reverse kernels: one warp per block while the grid is too small to
+// give every SM several blocks of four warps (an FP64-heavy warp keeps an SM's FP64 pipe busy
+// on its own), four warps otherwise.
+inline int block_threads(long long n) { return n < 152LL * 4 * 128 ? 32 : 128; }
+
 // Recompute the primitive states of every substep of segment q into the tape.
 void recompute_segment(hz_adjoint* a, int q, int* nsteps_out) {
   hz_ctx* c = a->ctx;
@@ -141,11 +146,12 @@ void launch_cell(hz_adjoint* a, const void* Pb, int stage, int gather) {
   sh.stage = stage;
   sh.gather = gather;
   const long long n = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
-  const int blocks = grid_blocks(n, 128);
+  const int threads = block_threads(n);
+  const int blocks = grid_blocks(n, threads);
   if (c->o.cleaning)
-    k_adj_cell<true><<<blocks, 128, 0, c->st>>>(c->kp, sh, (const double*)Pb, (const double*)c->met, a->bufs);
+    k_adj_cell<true><<<blocks, threads, 0, c->st>>>(c->kp, sh, (const double*)Pb, (const double*)c->met, a->bufs);
   else
-    k_adj_cell<false><<<blocks, 128, 0, c->st>>>(c->kp, sh, (const double*)Pb, (const double*)c->met, a->bufs);
+    k_adj_cell<false><<<blocks, threads, 0, c->st>>>(c->kp, sh, (const double*)Pb, (const double*)c->met, a->bufs);
 }
 
 void launch_face(hz_adjoint* a, const void* Ps) {
@@ -160,11 +166,12 @@ void launch_face(hz_adjoint* a, const void* Ps) {
     const long long nf = (long long)(c->g.n[0] + (d == 0)) * (c->g.n[1] + (d == 1)) * (c->g.n[2] + (d == 2));
     if (nf > nmax) nmax = nf;
   }
-  dim3 grid(grid_blocks(nmax, 128), a->A.ndir);
+  const int threads = block_threads(nmax);
+  dim3 grid(grid_blocks(nmax, threads), a->A.ndir);
   if (c->o.cleaning)
-    k_adj_face<true><<<grid, 128, 0, c->st>>>(c->kp, sh, (const double*)Ps, (const double*)c->met, a->bufs);
+    k_adj_face<true><<<grid, threads, 0, c->st>>>(c->kp, sh, (const double*)Ps, (const double*)c->met, a->bufs);
   else
-    k_adj_face<false><<<grid, 128, 0, c->st>>>(c->kp, sh, (const double*)Ps, (const double*)c->met, a->bufs);
+    k_adj_face<false><<<grid, threads, 0, c->st>>>(c->kp, sh, (const double*)Ps, (const double*)c->met, a->bufs);
 }
 
 }  // namespace

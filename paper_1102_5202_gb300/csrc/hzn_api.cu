@@ -130,7 +130,12 @@ Layout layout_of(const hz_grid* g, const hz_options* o) {
   L.met = round_up((size_t)L.ms * 10 * es, 256);
   L.u_bytes = (size_t)L.fs * NF * sizeof(double);
   L.p_bytes = round_up((size_t)L.fs * NF * es, 256);
-  L.total = L.scal + L.met + 2 * L.u_bytes + 2 * L.p_bytes;  // U0, U1, P[0], P[1]
+  // geometry tables of a DIAG metric: centre geometry; in FP64 also face geometry and source
+  // differences per active axis
+  const int ndims = gx + gy + gz;
+  const int ngeo = o->precision == HZ_MIXED ? GEO_N : GEO_N + ndims * (GEO_N + GEO_S);
+  L.geo = round_up((size_t)L.ms * ngeo * sizeof(double), 256);
+  L.total = L.scal + L.met + 2 * L.u_bytes + 2 * L.p_bytes + L.geo;  // U0, U1, P[0], P[1], tables
   return L;
 }
 
@@ -224,6 +229,7 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   c->U1 = (double*)(p + L.u_bytes);
   c->P[0] = (void*)(p + 2 * L.u_bytes);
   c->P[1] = (void*)(p + 2 * L.u_bytes + L.p_bytes);
+  double* geo = (double*)(p + 2 * L.u_bytes + 2 * L.p_bytes);
   c->cur = 0;
   c->v.dims = grid->n[2] > 1 ? 3 : (grid->n[1] > 1 ? 2 : 1);
   c->v.clean = opts->cleaning;
@@ -262,7 +268,14 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   kp.p_atm = patm < opts->p_floor ? opts->p_floor : patm;
   kp.c2p_maxit = opts->c2p_maxit;
   kp.c2p_tol = opts->c2p_tol;
+  kp.c2p_step_tol = 0.01 * sqrt(opts->c2p_tol);
   kp.c2p_1d = opts->c2p == HZ_C2P_1D;
+  {
+    const int ndims = kp.gx + kp.gy + kp.gz;
+    kp.geo_c = geo;
+    kp.geo_f = c->v.mixed ? nullptr : geo + GEO_N * L.ms;
+    kp.geo_s = c->v.mixed ? nullptr : geo + GEO_N * L.ms + (long long)ndims * GEO_N * L.ms;
+  }
   // z chunks: enough blocks for several waves on 152 SMs
   int tx, ty;
   tile_of(c->v.dims, &tx, &ty);
@@ -350,6 +363,11 @@ int hz_set_metric(hz_ctx* c, const double* d_metric) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return HZ_ERR_CUDA;
   c->v.diag = general ? 0 : 1;
+  if (c->v.diag) {
+    launch_geo_tables(c->v, c->kp, c->met, (double*)c->kp.geo_c, (double*)c->kp.geo_f,
+                      (double*)c->kp.geo_s, c->st);
+    if (cudaGetLastError() != cudaSuccess) return HZ_ERR_CUDA;
+  }
   c->have_metric = 1;
   return HZ_OK;
 }

@@ -29,9 +29,10 @@ struct hz_ctx {
 namespace hzn {
 
 // Workspace layout of one grid: device scalars, metric, two conserved and two primitive
-// arrays.  Grid functions are padded: rows of `pitch` elements, fields `fs` elements apart.
+// arrays, and the geometry tables of a DIAG metric (metric layout, FP64).  Grid functions are
+// padded: rows of `pitch` elements, fields `fs` elements apart.
 struct Layout {
-  size_t scal, met, u_bytes, p_bytes, total;
+  size_t scal, met, u_bytes, p_bytes, geo, total;
   long long fs, ms;
   int pitch, mpitch, mny;
   long long plane, mplane;

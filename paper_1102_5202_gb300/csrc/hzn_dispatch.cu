@@ -64,6 +64,14 @@ void launch_max_speed(const Variant& v, const KParams& kp, const void* P, const 
   }
 }
 
+void launch_geo_tables(const Variant& v, const KParams& kp, const void* M, double* geo_c,
+                       double* geo_f, double* geo_s, cudaStream_t st) {
+  const long long n = (long long)(kp.nx + 1) * (kp.ny + kp.gy) * (kp.nz + kp.gz);
+  const int nb = blocks_for(n, 256);
+  if (v.mixed) k_geo_tables<float><<<nb, 256, 0, st>>>(kp, (const float*)M, geo_c, geo_f, geo_s, 0);
+  else k_geo_tables<double><<<nb, 256, 0, st>>>(kp, (const double*)M, geo_c, geo_f, geo_s, 1);
+}
+
 void launch_prim2cons(const Variant& v, const KParams& kp, const void* P, const void* M, double* U,
                       cudaStream_t st) {
   if (v.mixed) launch_prim2cons_t<true>(v, kp, P, M, U, st);

@@ -61,6 +61,7 @@ struct EnsParams {
   double rho_floor, rho_atm, p_floor, atm_K;
   int c2p_maxit;
   double c2p_tol;
+  double c2p_step_tol;
 };
 
 // Flat-metric geometry (alpha = 1, beta = 0, gamma_ij = delta_ij).
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(NT, MINB) k_ensemble(const EnsParams ep) {
             // recovery with atmosphere / floors (same rules as the grid path)
             const bool atm = U[U_D] < ep.rho_atm;
             C2PResult r = {1, 0};
-            if (!atm) r = con2prim<false, true>(G, U, Pg, c, ep.c2p_maxit, ep.c2p_tol, Pn);
+            if (!atm) r = con2prim<false, true>(G, U, Pg, c, ep.c2p_maxit, ep.c2p_step_tol, Pn);
             maxit = max(maxit, r.iters);
             bool reset = false;
             if (atm || !r.ok || Pn[P_RHO] < ep.rho_floor) {
@@ -479,6 +480,7 @@ int hz_ensemble_create(hz_ensemble** out, int ntubes, const int* h_n, const doub
   e->ep.p_floor = opts->p_floor;
   e->ep.c2p_maxit = opts->c2p_maxit;
   e->ep.c2p_tol = opts->c2p_tol;
+  e->ep.c2p_step_tol = 0.01 * sqrt(opts->c2p_tol);
   // host tables
   std::vector<TubeInfo> ti(ntubes);
   std::vector<long long> cat(ntubes), pad(ntubes);

@@ -32,9 +32,23 @@ struct KParams {
   double rho_floor, rho_atm, p_floor, p_atm;
   int c2p_maxit;
   double c2p_tol;
+  double c2p_step_tol;   // Newton stops once a step is below this (0.01 sqrt(c2p_tol), relative)
   int c2p_1d;            // 1: the 1D recovery scheme (Newton in z, v^2 eliminated)
   int zlen;              // cells of z per block
+  // Geometry tables of a metric with zero shift and diagonal gamma (filled by hz_set_metric,
+  // used by the DIAG kernels), in the metric's padded layout (field stride ms):
+  //   geo_c  centre geometry, GEO_N fields (both precisions; FP64 values);
+  //   geo_f  face geometry of axis d at geo_f + d GEO_N ms, the face i - 1/2 of cell (i, j, k)
+  //          at the cell's metric offset (FP64 path only);
+  //   geo_s  differences g(+1) - g(-1) of g_tt, g_xx, g_yy, g_zz along axis d at
+  //          geo_s + d GEO_S ms (FP64 path only).
+  const double* geo_c;
+  const double* geo_f;
+  const double* geo_s;
 };
+
+constexpr int GEO_N = 10;  // alpha, 1/alpha, gamma_xx, _yy, _zz, gamma^xx, ^yy, ^zz, sqrt(gamma), sqrt(-g)
+constexpr int GEO_S = 4;   // g_tt, g_xx, g_yy, g_zz
 
 // One substep: Uout = a0 U0 + ak (Uk + dt L(Pin)); Pout = primitives of Uout.
 struct StageArgs {
@@ -63,10 +77,12 @@ void launch_prim2cons(const Variant& v, const KParams& kp, const void* P, const 
                       cudaStream_t st);
 void launch_max_speed(const Variant& v, const KParams& kp, const void* P, const void* M,
                       DevScalars* sc, cudaStream_t st);
+void launch_geo_tables(const Variant& v, const KParams& kp, const void* M, double* geo_c,
+                       double* geo_f, double* geo_s, cudaStream_t st);
 
 // Tile shape of the substep kernel per dimensionality.
 inline void tile_of(int dims, int* tx, int* ty) {
-  *tx = dims == 1 ? 128 : 32;
+  *tx = 32;
   *ty = dims == 1 ? 1 : 4;
 }
 

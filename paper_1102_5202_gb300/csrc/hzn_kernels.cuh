@@ -78,6 +78,44 @@ __device__ __forceinline__ void load_metric(const KParams& kp, const S* __restri
   }
 }
 
+// Geometry of a DIAG metric from a table written by k_geo_tables (the same values make_geom
+// computes from the metric).
+template <typename R>
+__device__ __forceinline__ Geom<R> geo_load(const double* __restrict__ g, long long off, long long ms) {
+  Geom<R> G;
+  G.alp = (R)__ldg(g + off);
+  G.ialp = (R)__ldg(g + ms + off);
+  G.gxx = (R)__ldg(g + 2 * ms + off);
+  G.gyy = (R)__ldg(g + 3 * ms + off);
+  G.gzz = (R)__ldg(g + 4 * ms + off);
+  G.ixx = (R)__ldg(g + 5 * ms + off);
+  G.iyy = (R)__ldg(g + 6 * ms + off);
+  G.izz = (R)__ldg(g + 7 * ms + off);
+  G.sqrtg = (R)__ldg(g + 8 * ms + off);
+  G.sqrtmg = (R)__ldg(g + 9 * ms + off);
+  G.bx = G.by = G.bz = R(0);
+  G.blx = G.bly = G.blz = R(0);
+  G.gxy = G.gxz = G.gyz = R(0);
+  G.ixy = G.ixz = G.iyz = R(0);
+  G.gtt = -G.alp * G.alp;
+  return G;
+}
+
+template <typename R>
+__device__ __forceinline__ void geo_store(double* __restrict__ g, long long off, long long ms,
+                                          const Geom<R>& G) {
+  g[off] = G.alp;
+  g[ms + off] = G.ialp;
+  g[2 * ms + off] = G.gxx;
+  g[3 * ms + off] = G.gyy;
+  g[4 * ms + off] = G.gzz;
+  g[5 * ms + off] = G.ixx;
+  g[6 * ms + off] = G.iyy;
+  g[7 * ms + off] = G.izz;
+  g[8 * ms + off] = G.sqrtg;
+  g[9 * ms + off] = G.sqrtmg;
+}
+
 // HLLE flux of the face at i - 1/2 along D of cell (i, j, k) (the face between cells i-1 and
 // i along D), written to out[f * ostride].
 // RECON 0: TVD with the MC limiter (stencil c-2 .. c+1); 1: PPM (stencil c-3 .. c+2).
@@ -112,9 +150,12 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
     }
   }
   if (!CLEAN) PL[8] = PR[8] = R(0);
-  // face metric: mean of the two adjacent centre values
-  R m[10];
-  {
+  // face metric: mean of the two adjacent centre values (tabulated for a DIAG metric in FP64)
+  Geom<R> G;
+  if constexpr (DIAG && sizeof(R) == sizeof(double)) {
+    G = geo_load<R>(kp.geo_f + D * GEO_N * kp.ms, met_off(kp, i, j, k), kp.ms);
+  } else {
+    R m[10];
     const long long o1 = met_off(kp, i, j, k);
     const long long o0 = o1 - (D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane));
     R m0[10], m1[10];
@@ -122,22 +163,36 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
     load_metric<DIAG>(kp, M, o1, m1);
 #pragma unroll
     for (int f = 0; f < 10; ++f) m[f] = R(0.5) * (m0[f] + m1[f]);
+    G = make_geom<DIAG>(m);
   }
-  const Geom<R> G = make_geom<DIAG>(m);
   const Consts<R> c = consts_of<R>(kp);
-  R FL[9], UL[9], lmL, lpL;
+  // wave speeds.  FP64: both states' quadratics, multiplied through by w (w + b^2), share one
+  // division 0.5 / (A'_L A'_R).  FP32 (mixed): the plain quadratic per state, since A' scales
+  // like w^2 and the product underflows FP32 in near-vacuum cells.
+  constexpr bool SHARED = sizeof(R) == sizeof(double);
+  R FL[9], UL[9], AL, BL, sqL, lmL, lpL;
   {
     const State<R> St = make_state<DIAG>(G, PL, c);
     flux_of<D, CLEAN, DIAG>(G, St, c, FL);
     cons_of<CLEAN>(G, St, UL);
-    speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmL, lpL);
+    if constexpr (SHARED) speed_quadratic<D, DIAG>(G, St, c, AL, BL, sqL);
+    else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmL, lpL);
   }
-  R FR[9], UR[9], lmR, lpR;
+  R FR[9], UR[9], AR, BR, sqR, lmR, lpR;
   {
     const State<R> St = make_state<DIAG>(G, PR, c);
     flux_of<D, CLEAN, DIAG>(G, St, c, FR);
     cons_of<CLEAN>(G, St, UR);
-    speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmR, lpR);
+    if constexpr (SHARED) speed_quadratic<D, DIAG>(G, St, c, AR, BR, sqR);
+    else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmR, lpR);
+  }
+  if constexpr (SHARED) {
+    const R ia = R(0.5) / (AL * AR);
+    const R i2aL = AR * ia, i2aR = AL * ia;
+    lpL = (-BL + sqL) * i2aL;
+    lmL = (-BL - sqL) * i2aL;
+    lpR = (-BR + sqR) * i2aR;
+    lmR = (-BR - sqR) * i2aR;
   }
   // HLLE: F = (sR FL - sL FR + sL sR (UR - UL)) / (sR - sL)
   const R sl = fmin(R(0), fmin(lmL, lmR));
@@ -307,34 +362,40 @@ __device__ __forceinline__ void block_stats(DevScalars* sc, double vloc, int nfa
   }
 }
 
-// Recovery with atmosphere / floor handling; rewrites U when the cell is reset.
-template <bool CLEAN, bool DIAG, bool ONE_FINISH = false>
+// Recovery with atmosphere / floor handling; rewrites U when the cell is reset.  TG, TP: the
+// element types of the guess and of the result (float for the mixed path, whose primitive
+// state is stored in FP32; a reset recomputes U from that stored state).
+template <bool CLEAN, bool DIAG, bool ONE_FINISH = false, typename TG = double, typename TP = double>
 __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G, double U[9],
-                                       const double Pg[9], const Consts<double>& c, double P[9],
+                                       const TG Pg[9], const Consts<double>& c, TP P[9],
                                        int& iters) {
   // atmosphere: a cell whose rest-mass density D / sqrt(gamma) = rho W is below rho_atm is not
   // recovered but set to the atmosphere state (the decision uses the conserved state only)
   const bool atm = U[U_D] < kp.rho_atm * G.sqrtg;
   C2PResult r = {1, 0};
-  if (!atm) r = con2prim<CLEAN, DIAG, ONE_FINISH>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_tol, P, kp.c2p_1d);
+  if (!atm)
+    r = con2prim<CLEAN, DIAG, ONE_FINISH, TG, TP>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_step_tol, P, kp.c2p_1d);
   iters = r.iters;
   bool reset = false;
-  if (atm || !r.ok || P[P_RHO] < kp.rho_floor) {
+  if (atm || !r.ok || (double)P[P_RHO] < kp.rho_floor) {
     const double isg = 1.0 / G.sqrtmg;
-    P[P_BX] = U[U_BX] * isg;
-    P[P_BY] = U[U_BY] * isg;
-    P[P_BZ] = U[U_BZ] * isg;
-    P[P_PSI] = CLEAN ? U[U_PSI] / G.sqrtg : 0.0;
-    P[P_RHO] = kp.rho_floor;
-    P[P_PRS] = kp.p_atm;
-    P[P_UX] = P[P_UY] = P[P_UZ] = 0.0;
+    P[P_BX] = (TP)(U[U_BX] * isg);
+    P[P_BY] = (TP)(U[U_BY] * isg);
+    P[P_BZ] = (TP)(U[U_BZ] * isg);
+    P[P_PSI] = CLEAN ? (TP)(U[U_PSI] / G.sqrtg) : TP(0);
+    P[P_RHO] = (TP)kp.rho_floor;
+    P[P_PRS] = (TP)kp.p_atm;
+    P[P_UX] = P[P_UY] = P[P_UZ] = TP(0);
     reset = true;
-  } else if (P[P_PRS] < kp.p_floor) {
-    P[P_PRS] = kp.p_floor;
+  } else if ((double)P[P_PRS] < kp.p_floor) {
+    P[P_PRS] = (TP)kp.p_floor;
     reset = true;
   }
   if (reset) {
-    const State<double> S = make_state<DIAG>(G, P, c);
+    double Pd[9];
+#pragma unroll
+    for (int f = 0; f < 9; ++f) Pd[f] = (double)P[f];
+    const State<double> S = make_state<DIAG>(G, Pd, c);
     cons_of<CLEAN>(G, S, U);
   }
   return r.ok ? 0 : 1;
@@ -405,9 +466,14 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         L[f] = v;
       }
       // metric source 1/2 sqrt(-g) T^{ab} d_i g_ab (static metric: no energy source)
-      R mc[10];
-      load_metric<DIAG>(kp, M, mo, mc);
-      const Geom<R> G = make_geom<DIAG>(mc);
+      Geom<R> G;
+      if constexpr (DIAG && !MIXED) {
+        G = geo_load<R>(kp.geo_c, mo, kp.ms);
+      } else {
+        R mc[10];
+        load_metric<DIAG>(kp, M, mo, mc);
+        G = make_geom<DIAG>(mc);
+      }
       R Pc[9];
 #pragma unroll
       for (int f = 0; f < NV; ++f) Pc[f] = (R)__ldg(P + f * kp.fs + off);
@@ -416,17 +482,31 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         const State<R> St = make_state<DIAG>(G, Pc, c);
         const Tup<R> T = tup_of<DIAG>(G, St);
         const R h = R(0.5) * G.sqrtmg;
-        {
-          const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + 1), gm = g4_at<DIAG, R>(kp, M, mo - 1);
-          L[U_TX] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idx);
-        }
-        if (YA) {
-          const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + kp.mpitch), gm = g4_at<DIAG, R>(kp, M, mo - kp.mpitch);
-          L[U_TY] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idy);
-        }
-        if (ZA) {
-          const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + kp.mplane), gm = g4_at<DIAG, R>(kp, M, mo - kp.mplane);
-          L[U_TZ] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idz);
+        if constexpr (DIAG && !MIXED) {
+          // tabulated differences of g_tt, g_xx, g_yy, g_zz between the two neighbours
+          const double* gs = kp.geo_s;
+          const long long ms = kp.ms;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            if ((d == 1 && !YA) || (d == 2 && !ZA)) continue;
+            const double* g = gs + d * GEO_S * ms + mo;
+            const R s = T.tt * (R)__ldg(g) + T.xx * (R)__ldg(g + ms) + T.yy * (R)__ldg(g + 2 * ms) +
+                        T.zz * (R)__ldg(g + 3 * ms);
+            L[U_TX + d] += h * s * (R)(0.5 * (d == 0 ? kp.idx : (d == 1 ? kp.idy : kp.idz)));
+          }
+        } else {
+          {
+            const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + 1), gm = g4_at<DIAG, R>(kp, M, mo - 1);
+            L[U_TX] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idx);
+          }
+          if (YA) {
+            const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + kp.mpitch), gm = g4_at<DIAG, R>(kp, M, mo - kp.mpitch);
+            L[U_TY] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idy);
+          }
+          if (ZA) {
+            const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + kp.mplane), gm = g4_at<DIAG, R>(kp, M, mo - kp.mplane);
+            L[U_TZ] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idz);
+          }
         }
         if (CLEAN) L[U_PSI] += -(R)kp.kappa * G.alp * (G.sqrtg * St.psi);
       }
@@ -440,18 +520,22 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         U[f] = u;
       }
       if (!CLEAN) U[8] = 0.0;
-      // recovery of the new primitive state (FP64)
-      double Pg[9], Pn[9];
-#pragma unroll
-      for (int f = 0; f < 9; ++f) Pg[f] = (double)Pc[f];
+      // recovery of the new primitive state (FP64 Newton; the mixed path forms its guess and
+      // the FP32-stored part of its result in FP32)
       int it;
+      R Pn[9];
       if constexpr (MIXED) {
-        double md[10];
-        load_metric<DIAG>(kp, M, mo, md);
-        const Geom<double> Gd = make_geom<DIAG>(md);
-        nfail += recover<CLEAN, DIAG, true>(kp, Gd, U, Pg, cd, Pn, it);
+        Geom<double> Gd;
+        if constexpr (DIAG) {
+          Gd = geo_load<double>(kp.geo_c, mo, kp.ms);
+        } else {
+          double md[10];
+          load_metric<DIAG>(kp, M, mo, md);
+          Gd = make_geom<DIAG>(md);
+        }
+        nfail += recover<CLEAN, DIAG, true, R, R>(kp, Gd, U, Pc, cd, Pn, it);
       } else {
-        nfail += recover<CLEAN, DIAG>(kp, G, U, Pg, cd, Pn, it);
+        nfail += recover<CLEAN, DIAG>(kp, G, U, Pc, cd, Pn, it);
       }
       maxit = max(maxit, it);
 #pragma unroll
@@ -459,12 +543,7 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         sa.Uout[f * kp.fs + off] = U[f];
         Pout[f * kp.fs + off] = (S)Pn[f];
       }
-      if (sa.last) {
-        R Pr[9];
-#pragma unroll
-        for (int f = 0; f < 9; ++f) Pr[f] = (R)(S)Pn[f];
-        vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pr, c));
-      }
+      if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pn, c));
     }
     __syncthreads();
   }
@@ -522,7 +601,7 @@ __global__ void __launch_bounds__(256) k_max_speed(const KParams kp, const typen
   block_stats<256>(sc, v, 0, 0, true);
 }
 
-inline int grid_blocks(long long n, int threads) {
+inline int blocks_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152 * 16) b = 152 * 16;
   if (b < 1) b = 1;
@@ -533,7 +612,10 @@ inline int grid_blocks(long long n, int threads) {
 template <bool YA, bool ZA, bool MIXED, int RECON>
 void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, const void* Mv,
                       DevScalars* sc, int zchunks, cudaStream_t st) {
-  constexpr int TX = (!YA && !ZA) ? 128 : 32;
+  // 1-D: one warp of cells per block, so that a short tube spreads over many SMs (each FP64
+  // warp instruction occupies an SM's FP64 pipe for 16 cycles; several warps of one block on
+  // one SM would serialise)
+  constexpr int TX = 32;
   constexpr int TY = (!YA && !ZA) ? 1 : 4;
   using S = typename Prec<MIXED>::S;
   const S* M = (const S*)Mv;
@@ -547,6 +629,53 @@ void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, 
   }
 }
 
+// Geometry tables of a DIAG metric (see KParams): one thread per point of the padded metric
+// layout; the same arithmetic as the kernels' own make_geom of the centre and face metrics.
+template <typename S>
+__global__ void k_geo_tables(const KParams kp, const S* __restrict__ M, double* __restrict__ gc,
+                             double* __restrict__ gf, double* __restrict__ gs, int faces) {
+  const int ya = kp.gy, za = kp.gz;
+  const long long n = (long long)(kp.nx + 1) * (kp.ny + ya) * (kp.nz + za);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % (kp.nx + 1));
+    const int j = (int)((q / (kp.nx + 1)) % (kp.ny + ya));
+    const int k = (int)(q / ((long long)(kp.nx + 1) * (kp.ny + ya)));
+    const long long mo = met_off(kp, i, j, k);
+    const bool cell = i < kp.nx && j < kp.ny && k < kp.nz;
+    if (cell) {
+      double m[10];
+      load_metric<true>(kp, M, mo, m);
+      geo_store(gc, mo, kp.ms, make_geom<true>(m));
+    }
+    if (!faces) continue;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if ((d == 1 && !ya) || (d == 2 && !za)) continue;
+      // face i - 1/2 along d: needs the index along d in [0, n_d], the others inside
+      const bool fin = (d == 0 ? i <= kp.nx : i < kp.nx) && (d == 1 ? j <= kp.ny : j < kp.ny) &&
+                       (d == 2 ? k <= kp.nz : k < kp.nz);
+      const long long st = d == 0 ? 1 : (d == 1 ? kp.mpitch : kp.mplane);
+      if (fin) {
+        double m0[10], m1[10], m[10];
+        load_metric<true>(kp, M, mo - st, m0);
+        load_metric<true>(kp, M, mo, m1);
+#pragma unroll
+        for (int f = 0; f < 10; ++f) m[f] = 0.5 * (m0[f] + m1[f]);
+        geo_store(gf + d * GEO_N * kp.ms, mo, kp.ms, make_geom<true>(m));
+      }
+      if (cell) {
+        const G4<double> gp = g4_at<true, double>(kp, M, mo + st), gm = g4_at<true, double>(kp, M, mo - st);
+        double* g = gs + d * GEO_S * kp.ms + mo;
+        g[0] = gp.gtt - gm.gtt;
+        g[kp.ms] = gp.gxx - gm.gxx;
+        g[2 * kp.ms] = gp.gyy - gm.gyy;
+        g[3 * kp.ms] = gp.gzz - gm.gzz;
+      }
+    }
+  }
+}
+
 template <bool YA, bool ZA, bool MIXED>
 void launch_max_speed_t(const Variant& v, const KParams& kp, const void* Pv, const void* Mv,
                         DevScalars* sc, cudaStream_t st) {
@@ -554,7 +683,7 @@ void launch_max_speed_t(const Variant& v, const KParams& kp, const void* Pv, con
   const S* P = (const S*)Pv;
   const S* M = (const S*)Mv;
   const long long n = (long long)kp.nx * kp.ny * kp.nz;
-  const int nb = grid_blocks(n, 256);
+  const int nb = blocks_for(n, 256);
   if (v.clean) {
     if (v.diag) k_max_speed<YA, ZA, true, true, MIXED><<<nb, 256, 0, st>>>(kp, P, M, sc);
     else k_max_speed<YA, ZA, true, false, MIXED><<<nb, 256, 0, st>>>(kp, P, M, sc);
@@ -571,7 +700,7 @@ void launch_prim2cons_t(const Variant& v, const KParams& kp, const void* Pv, con
   const S* P = (const S*)Pv;
   const S* M = (const S*)Mv;
   const long long n = (long long)kp.nx * kp.ny * kp.nz;
-  const int nb = grid_blocks(n, 256);
+  const int nb = blocks_for(n, 256);
   if (v.clean) {
     if (v.diag) k_prim2cons<true, true, MIXED><<<nb, 256, 0, st>>>(kp, P, M, U);
     else k_prim2cons<true, false, MIXED><<<nb, 256, 0, st>>>(kp, P, M, U);

@@ -259,6 +259,36 @@ __device__ __forceinline__ void speeds_of(const Geom<R>& G, const State<R>& S, R
   lm = (-B - sq) * i2a;
 }
 
+// The same quadratic multiplied through by w (w + b^2), so that c^2 = N / Dd enters without a
+// division: A' = (Dd - N) (u^t)^2 + N / alpha^2, B', C' likewise; its roots are the speeds.
+// Returns A', B' and sqrt(max(B'^2 - 4 A'C', 0)); lambda+- = (-B' +- sq) / (2 A').
+template <int D, bool DIAG, typename R>
+__device__ __forceinline__ void speed_quadratic(const Geom<R>& G, const State<R>& S, const Consts<R>& c,
+                                                R& A, R& B, R& sq) {
+  const R gp = c.gamma * S.p;
+  const R wt = S.w + S.b2;
+  const R N = gp * wt + S.b2 * (S.w - gp);
+  const R Dd = S.w * wt;
+  const R ia2 = G.ialp * G.ialp;
+  const R ud = sel<D>(S.ux, S.uy, S.uz);
+  const R oc = Dd - N;
+  A = oc * S.ut * S.ut + N * ia2;
+  R C;
+  if constexpr (DIAG) {
+    B = R(-2) * (oc * S.ut * ud);
+    C = oc * ud * ud - N * sel<D>(G.ixx, G.iyy, G.izz);
+  } else {
+    const R bd = sel<D>(G.bx, G.by, G.bz);
+    const R gtd = bd * ia2;
+    const R gdd = sel<D>(G.ixx, G.iyy, G.izz) - bd * bd * ia2;
+    B = R(-2) * (oc * S.ut * ud - N * gtd);
+    C = oc * ud * ud - N * gdd;
+  }
+  R disc = B * B - R(4) * A * C;
+  disc = disc > R(0) ? disc : R(0);
+  sq = sqrt(disc);
+}
+
 // Coordinate speeds of the cleaning pair along D: -beta^D -+ c_h alpha sqrt(gamma^DD).
 template <int D, bool DIAG, typename R>
 __device__ __forceinline__ void clean_speeds(const Geom<R>& G, R ch, R& lm, R& lp) {
@@ -447,29 +477,46 @@ static __device__ __noinline__ bool c2p_bracketed(const C2PScalars q, double zgu
   return true;
 }
 
-// Guarded Newton update: keep z > 0 and 0 <= v^2 < 1.
+// Guarded Newton update: keep z > 0 and 0 <= v^2 < 1.  Returns false when the step had to be
+// replaced by halving the distance to the bound z = 0 or v^2 = 1: a run of such steps shrinks
+// geometrically without converging, so it may not end the iteration.  A step below v^2 = 0 is
+// projected onto it and counts as a plain step (gas at rest has its root there).
 template <typename R>
-__device__ __forceinline__ void c2p_apply(R& z, R& v2, NewtonStep<R> st) {
+__device__ __forceinline__ bool c2p_apply(R& z, R& v2, NewtonStep<R> st) {
   R zn = z + st.dz;
   R vn = v2 + st.dv;
-  if (!(zn > R(0))) zn = R(0.5) * z;
+  bool plain = true;
+  if (!(zn > R(0))) {
+    zn = R(0.5) * z;
+    plain = false;
+  }
   if (vn < R(0)) vn = R(0);
-  if (!(vn < R(1))) vn = R(0.5) * (v2 + R(1));
+  if (!(vn < R(1))) {
+    vn = R(0.5) * (v2 + R(1));
+    plain = false;
+  }
   z = zn;
   v2 = vn;
+  return plain;
 }
 
 // Recovery at one cell.  G is the FP64 centre geometry; U the FP64 conserved vector; Pg the
-// previous primitive state (initial guess).  maxit caps the FP64 iterations.  ONE_FINISH:
+// previous primitive state (initial guess).  maxit caps the FP64 iterations; they stop once a
+// Newton step is below step_tol (relative in z, absolute in v^2): the iteration converges
+// quadratically there, so the error left is about the square of that step.  ONE_FINISH:
 // when the FP32 stage has settled, apply a single FP64 Newton correction (quadratic
 // convergence takes the 1e-7 FP32 error to ~1e-14, ample when the result is stored in FP32).
 //
 // one_d: the 1D scheme instead (§3.2 names a 1D and a 2D recovery): Newton in z alone with v^2
 // eliminated, from the previous state's z, kept in its bracket by bisection (c2p_bracketed).
-template <bool CLEAN, bool DIAG, bool ONE_FINISH = false>
+//
+// TG, TP: element types of the guess and of the result.  float for the mixed path, whose
+// primitive state is stored in FP32: the guess is formed in FP32, and of the result only the
+// pressure (a difference of nearly equal terms in cold gas) is formed in FP64.
+template <bool CLEAN, bool DIAG, bool ONE_FINISH = false, typename TG = double, typename TP = double>
 __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const double U[9],
-                                              const double Pg[9], const Consts<double>& c,
-                                              int maxit, double tol, double P[9], int one_d = 0) {
+                                              const TG Pg[9], const Consts<double>& c,
+                                              int maxit, double step_tol, TP P[9], int one_d = 0) {
   const double isg = 1.0 / G.sqrtg;
   const double Dd = U[U_D] * isg;
   const double Sx = U[U_TX] * isg, Sy = U[U_TY] * isg, Sz = U[U_TZ] * isg;
@@ -513,15 +560,17 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
   // initial guess from the previous primitive state: z = w W^2 / D, v^2 = uu / (1 + uu)
   double z, v2;
   {
-    const double vx = Pg[P_UX], vy = Pg[P_UY], vz = Pg[P_UZ];
-    double uu;
-    if constexpr (DIAG) uu = G.gxx * vx * vx + G.gyy * vy * vy + G.gzz * vz * vz;
+    using T = TG;
+    const T vx = Pg[P_UX], vy = Pg[P_UY], vz = Pg[P_UZ];
+    T uu;
+    if constexpr (DIAG) uu = (T)G.gxx * vx * vx + (T)G.gyy * vy * vy + (T)G.gzz * vz * vz;
     else
-      uu = (G.gxx * vx + G.gxy * vy + G.gxz * vz) * vx + (G.gxy * vx + G.gyy * vy + G.gyz * vz) * vy +
-           (G.gxz * vx + G.gyz * vy + G.gzz * vz) * vz;
-    const double wg = Pg[P_RHO] + c.gfac * Pg[P_PRS];
-    z = wg * (1.0 + uu) * iD;
-    v2 = uu / (1.0 + uu);
+      uu = ((T)G.gxx * vx + (T)G.gxy * vy + (T)G.gxz * vz) * vx +
+           ((T)G.gxy * vx + (T)G.gyy * vy + (T)G.gyz * vz) * vy +
+           ((T)G.gxz * vx + (T)G.gyz * vy + (T)G.gzz * vz) * vz;
+    const T wg = Pg[P_RHO] + (T)c.gfac * Pg[P_PRS];
+    z = (double)(wg * (T(1) + uu) * (T)iD);
+    v2 = (double)(uu / (T(1) + uu));
     if (!(z > 0.0) || !(z < 1e30)) z = q.e;
   }
   bool settled = false;
@@ -536,9 +585,9 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
     const float ef = (float)q.e, sf = (float)q.s, qf = (float)q.q, bf = (float)q.b, gf = (float)g1;
     for (int it = 0; it < 30; ++it) {
       const NewtonStep<float> st = c2p_newton<float>(zf, vf, ef, sf, qf, bf, gf);
-      c2p_apply(zf, vf, st);
+      const bool plain = c2p_apply(zf, vf, st);
       ++res.iters;
-      if (fabsf(st.dz) <= 3e-6f * zf && fabsf(st.dv) <= 3e-6f) {
+      if (plain && fabsf(st.dz) <= 3e-6f * zf && fabsf(st.dv) <= 3e-6f) {
         settled = true;
         break;
       }
@@ -553,15 +602,15 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
   // FP64 stage
   if (!done && ONE_FINISH && settled) {
     const NewtonStep<double> st = c2p_newton<double>(z, v2, q.e, q.s, q.q, q.b, g1);
-    c2p_apply(z, v2, st);
+    const bool plain = c2p_apply(z, v2, st);
     ++res.iters;
-    done = fabs(st.dz) <= 1e-5 * z && fabs(st.dv) <= 1e-5;
+    done = plain && fabs(st.dz) <= 1e-5 * z && fabs(st.dv) <= 1e-5;
   }
   for (int it = 0; !done && it < maxit; ++it) {
     const NewtonStep<double> st = c2p_newton<double>(z, v2, q.e, q.s, q.q, q.b, g1);
-    c2p_apply(z, v2, st);
+    const bool plain = c2p_apply(z, v2, st);
     ++res.iters;
-    if (fabs(st.dz) <= tol * z && fabs(st.dv) <= tol) {
+    if (plain && fabs(st.dz) <= step_tol * z && fabs(st.dv) <= step_tol) {
       done = true;
       break;
     }
@@ -570,20 +619,38 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
     if (!c2p_bracketed(q, z, z, v2, res.iters)) return res;
   }
   const double rW = sqrt(1.0 - v2);  // 1/W
-  const double W = 1.0 / rW;
   const double Z = z * Dd;
   const double p = g1 * (Z * (1.0 - v2) - Dd * rW);
-  const double iZB = 1.0 / (Z + B2);
-  const double sbz = SB / Z;
-  P[P_RHO] = Dd * rW;
-  P[P_PRS] = p;
-  P[P_UX] = W * (Sux + sbz * Bx) * iZB;
-  P[P_UY] = W * (Suy + sbz * By) * iZB;
-  P[P_UZ] = W * (Suz + sbz * Bz) * iZB;
-  P[P_BX] = Bx * G.ialp;
-  P[P_BY] = By * G.ialp;
-  P[P_BZ] = Bz * G.ialp;
-  P[P_PSI] = CLEAN ? U[U_PSI] * isg : 0.0;
+  if constexpr (sizeof(TP) == sizeof(double)) {
+    const double W = 1.0 / rW;
+    const double iZB = 1.0 / (Z + B2);
+    const double sbz = SB / Z;
+    P[P_RHO] = Dd * rW;
+    P[P_PRS] = p;
+    P[P_UX] = W * (Sux + sbz * Bx) * iZB;
+    P[P_UY] = W * (Suy + sbz * By) * iZB;
+    P[P_UZ] = W * (Suz + sbz * Bz) * iZB;
+    P[P_BX] = Bx * G.ialp;
+    P[P_BY] = By * G.ialp;
+    P[P_BZ] = Bz * G.ialp;
+    P[P_PSI] = CLEAN ? U[U_PSI] * isg : 0.0;
+  } else {
+    // result stored in FP32: everything but p from FP32 copies of the FP64 quantities
+    const TP rWf = (TP)rW, Zf = (TP)Z, ia = (TP)G.ialp;
+    const TP Bxf = (TP)Bx, Byf = (TP)By, Bzf = (TP)Bz;
+    const TP W = TP(1) / rWf;
+    const TP iZB = TP(1) / (Zf + (TP)B2);
+    const TP sbz = (TP)SB / Zf;
+    P[P_RHO] = (TP)Dd * rWf;
+    P[P_PRS] = (TP)p;
+    P[P_UX] = W * ((TP)Sux + sbz * Bxf) * iZB;
+    P[P_UY] = W * ((TP)Suy + sbz * Byf) * iZB;
+    P[P_UZ] = W * ((TP)Suz + sbz * Bzf) * iZB;
+    P[P_BX] = Bxf * ia;
+    P[P_BY] = Byf * ia;
+    P[P_BZ] = Bzf * ia;
+    P[P_PSI] = CLEAN ? (TP)(U[U_PSI] * isg) : TP(0);
+  }
   res.ok = 1;
   return res;
 }

@@ -59,3 +59,20 @@ def test_ensemble_workspace_and_errors():
         hzn.hz_ensemble_workspace_bytes([1, 5])
     nb = hzn.hz_ensemble_workspace_bytes([200, 4000])
     assert nb >= 4 * 9 * (224 + 4000) * 8
+
+
+def test_full_ensemble_recovers_nearly_every_cell():
+    """The whole 512-tube workload (seed 1103) to t = 0.4: its strongest tubes (pressure ratios
+    up to 1e3, |B| up to 3.5 against rho down to 0.01) push a few cells against the recovery's
+    limits, and those are reset to the atmosphere; they stay a vanishing fraction of the zone
+    updates (a recovery that accepts a guarded, non-converged Newton step resets millions)."""
+    tubes = W.ensemble(512, seed=1103)
+    E = hzn.Ensemble(tubes)
+    E.run(0.4, 0.5, use_graph=False)
+    E.stream.synchronize()
+    t, steps, fails = E.results()
+    zu = float((E.n.astype(np.float64) * steps).sum())
+    assert np.all(t >= 0.4 - 1e-12)
+    assert fails.sum() <= 1e-5 * zu, (int(fails.sum()), zu)
+    print(f"512 tubes: {int(fails.sum())} recovery resets in {zu:.3e} zone updates")
+    E.close()

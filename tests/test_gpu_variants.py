@@ -32,6 +32,13 @@ def _ppm(P):
     return P
 
 
+# End-of-run bar of the PPM tubes.  PPM's monotonicity tests switch on products of neighbour
+# differences, so over 300 steps they amplify rounding-level differences between the two sides
+# more than MC does: Balsara 1 ends at 7e-9 with one evaluation order of the wave speeds and at
+# 1.15e-8 with another that differs by an ulp (Sod: 2.5e-10).  One step stays at 1e-10.
+TOL_END_PPM = 3e-8
+
+
 @pytest.mark.parametrize("case", ["balsara1", "sod"])
 def test_ppm_tubes_one_step_and_end(case):
     P = _ppm(W.balsara1(400) if case == "balsara1" else W.sod(400))
@@ -43,7 +50,7 @@ def test_ppm_tubes_one_step_and_end(case):
     gp, _, gs = gpu_run(P, t_end=0.4, cfl=0.5)
     op, _, os_ = oracle_run(P, t_end=0.4, cfl=0.5)
     assert gs["steps"] == os_["steps"]
-    r = assert_parity(gp, op, TOL_END, fields=range(8), what=f"{case} PPM t=0.4")
+    r = assert_parity(gp, op, TOL_END_PPM, fields=range(8), what=f"{case} PPM t=0.4")
     print(f"{case} PPM vs oracle at t=0.4 ({gs['steps']} steps): worst field rel L1 {r[:8].max():.1e}")
 
 

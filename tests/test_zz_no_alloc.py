@@ -86,5 +86,5 @@ def test_noalloc_rejects_grids_beyond_the_scratch():
     with pytest.raises(hzn.HznError) as e:
         hzn.hz_step_noalloc(big, opts, 256, 256, 256, 0.1, 1, 0)
     assert e.value.code == hzn.HZ_ERR_TOO_LARGE
-    fits = hzn.make_grid((32, 32, 32), (0.1, 0.1, 0.1), (0, 0, 0))
+    fits = hzn.make_grid((24, 24, 24), (0.1, 0.1, 0.1), (0, 0, 0))
     assert hzn.hz_workspace_bytes(fits, opts) <= hzn.HZ_NOALLOC_SCRATCH_BYTES
