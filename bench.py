@@ -38,16 +38,17 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # (profiles/fp64_alu_peak.md): 2 DFMA per clock per SM x 152 SMs.
 FP64_PEAK_TFLOPS = 1.194
 # FP64 operations per cell per substep executed by the fused substep kernel (3-D, cleaning
-# on), from ncu instruction counters on the 128^3 blob (profiles/k_substep_blob3d.md):
-# DFMA counted as 2 flops, DADD/DMUL as 1.
-FP64_FLOPS_PER_CELL_SUBSTEP = 2547.9
+# on, diagonal metric with its geometry tables), from ncu instruction counters on the 128^3
+# blob (profiles/k_substep_blob3d.md): DFMA counted as 2 flops, DADD/DMUL as 1.
+FP64_FLOPS_PER_CELL_SUBSTEP = 2194.3
 # DRAM bytes per cell per substep of the same kernel from the same capture (read + write,
-# 683.8 MB per launch at 128^3), scaled to a full launch by the cell count.
-DRAM_BYTES_PER_CELL_SUBSTEP = 326.1
-# The same two figures for the mixed-precision substep kernel (profiles/k_substep_mixed_blob3d.md):
-# FP64 flops (recovery, update) per cell per substep, and DRAM bytes per cell per substep.
-MIXED_FP64_FLOPS_PER_CELL_SUBSTEP = 202.2
-MIXED_DRAM_BYTES_PER_CELL_SUBSTEP = None
+# 1501 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
+DRAM_BYTES_PER_CELL_SUBSTEP = 715.9
+# The same two figures for the mixed-precision substep kernel at 256^3
+# (profiles/k_substep_mixed_blob3d.md): FP64 flops (recovery, update) per cell per substep,
+# and DRAM bytes per cell per substep.
+MIXED_FP64_FLOPS_PER_CELL_SUBSTEP = 157.6
+MIXED_DRAM_BYTES_PER_CELL_SUBSTEP = 318.0
 # Algorithmic HBM bytes per zone update (three substeps, FP64, nine fields): read P, U_k, U0,
 # metric and write U_{k+1}, P_{k+1} once per substep; stage 1 reads U0 once.
 HBM_BYTES_PER_ZU = (46 + 55 + 55) * 8
@@ -213,7 +214,7 @@ def run_gpu(args, rank, world, local):
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": DRAM_BYTES_PER_CELL_SUBSTEP * cells if DRAM_BYTES_PER_CELL_SUBSTEP else None,
-                "kernel": "k_substep<32,4,3-D,cleaning>", "peak_source": "measured FP64 DFMA loop"}
+                "kernel": "k_substep<32,4,3-D,cleaning,diag,FP64,MC>", "peak_source": "measured FP64 DFMA loop"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "kernel": "k_substep<32,4,3-D,cleaning>"}
