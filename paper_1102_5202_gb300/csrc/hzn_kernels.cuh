@@ -173,16 +173,16 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
   R FL[9], UL[9], AL, BL, sqL, lmL, lpL;
   {
     const State<R> St = make_state<DIAG>(G, PL, c);
-    flux_of<D, CLEAN, DIAG>(G, St, c, FL);
-    cons_of<CLEAN>(G, St, UL);
+    flux_of<D, CLEAN, DIAG, true>(G, St, c, FL);
+    cons_of<CLEAN, true>(G, St, UL);
     if constexpr (SHARED) speed_quadratic<D, DIAG>(G, St, c, AL, BL, sqL);
     else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmL, lpL);
   }
   R FR[9], UR[9], AR, BR, sqR, lmR, lpR;
   {
     const State<R> St = make_state<DIAG>(G, PR, c);
-    flux_of<D, CLEAN, DIAG>(G, St, c, FR);
-    cons_of<CLEAN>(G, St, UR);
+    flux_of<D, CLEAN, DIAG, true>(G, St, c, FR);
+    cons_of<CLEAN, true>(G, St, UR);
     if constexpr (SHARED) speed_quadratic<D, DIAG>(G, St, c, AR, BR, sqR);
     else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmR, lpR);
   }
@@ -194,18 +194,19 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
     lpR = (-BR + sqR) * i2aR;
     lmR = (-BR - sqR) * i2aR;
   }
-  // HLLE: F = (sR FL - sL FR + sL sR (UR - UL)) / (sR - sL)
+  // HLLE: F = (sR FL - sL FR + sL sR (UR - UL)) / (sR - sL).  FL, FR, UL, UR are the vectors
+  // divided by sqrt(-g) (the face's, common to both states), folded back into the weights.
   const R sl = fmin(R(0), fmin(lmL, lmR));
   const R sr = fmax(R(0), fmax(lpL, lpR));
   const R den = sr - sl;
   R wl, wr, wu;
   if (den != R(0)) {
-    const R iden = R(1) / den;
+    const R iden = G.sqrtmg / den;
     wl = sr * iden;
     wr = -sl * iden;
     wu = sl * sr * iden;
   } else {
-    wl = wr = R(0.5);
+    wl = wr = R(0.5) * G.sqrtmg;
     wu = R(0);
   }
 #pragma unroll
@@ -217,7 +218,7 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
     const R cden = csr - csl;
     const int fb = U_BX + D;
     if (cden != R(0)) {
-      const R ic = R(1) / cden;
+      const R ic = G.sqrtmg / cden;
       out[fb * ostride] = (csr * FL[fb] - csl * FR[fb] + csl * csr * (UR[fb] - UL[fb])) * ic;
       out[U_PSI * ostride] = (csr * FL[U_PSI] - csl * FR[U_PSI] + csl * csr * (UR[U_PSI] - UL[U_PSI])) * ic;
     }

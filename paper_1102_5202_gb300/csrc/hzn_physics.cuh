@@ -171,54 +171,59 @@ __device__ __forceinline__ State<R> make_state(const Geom<R>& G, const R P[9], c
   return S;
 }
 
-// Conserved vector w(u) (§2.2), with Psi = sqrt(gamma) psi.
-template <bool CLEAN, typename R>
+// Conserved vector w(u) (§2.2), with Psi = sqrt(gamma) psi.  UNSCALED: the vector divided by
+// sqrt(-g) (Psi by sqrt(-g) as well, i.e. psi / alpha); a face flux scales once at the end.
+template <bool CLEAN, bool UNSCALED = false, typename R>
 __device__ __forceinline__ void cons_of(const Geom<R>& G, const State<R>& S, R U[9]) {
+  const R sg = UNSCALED ? R(1) : G.sqrtmg;
   const R wt = S.w + S.b2, pt = S.p + R(0.5) * S.b2;
   const R a = wt * S.ut;
-  U[U_D] = G.sqrtmg * S.rho * S.ut;
-  U[U_TT] = G.sqrtmg * (a * S.l_t + pt - S.bt * S.b_t);
-  U[U_TX] = G.sqrtmg * (a * S.lx - S.bt * S.b_x);
-  U[U_TY] = G.sqrtmg * (a * S.ly - S.bt * S.b_y);
-  U[U_TZ] = G.sqrtmg * (a * S.lz - S.bt * S.b_z);
-  U[U_BX] = G.sqrtmg * S.Bx;
-  U[U_BY] = G.sqrtmg * S.By;
-  U[U_BZ] = G.sqrtmg * S.Bz;
-  if (CLEAN) U[U_PSI] = G.sqrtg * S.psi;
+  U[U_D] = sg * S.rho * S.ut;
+  U[U_TT] = sg * (a * S.l_t + pt - S.bt * S.b_t);
+  U[U_TX] = sg * (a * S.lx - S.bt * S.b_x);
+  U[U_TY] = sg * (a * S.ly - S.bt * S.b_y);
+  U[U_TZ] = sg * (a * S.lz - S.bt * S.b_z);
+  U[U_BX] = sg * S.Bx;
+  U[U_BY] = sg * S.By;
+  U[U_BZ] = sg * S.Bz;
+  if (CLEAN) U[U_PSI] = (UNSCALED ? G.ialp : G.sqrtg) * S.psi;
 }
 
 // Flux vector along D (§2.1 Eq. 2): sqrt(-g) rho u^D, sqrt(-g) T^D_nu, and the induction flux
 // sqrt(-g)(b^j u^D - b^D u^j) = sqrt(-g)(B^j u^D - B^D u^j) / u^t; cleaning adds
 // sqrt(-g) gamma^{Dj} psi to B^j and sqrt(gamma)(c_h^2 alpha^2 B^D - beta^D psi) on Psi.
-template <int D, bool CLEAN, bool DIAG, typename R>
+// UNSCALED: the flux divided by sqrt(-g), as for cons_of.
+template <int D, bool CLEAN, bool DIAG, bool UNSCALED = false, typename R>
 __device__ __forceinline__ void flux_of(const Geom<R>& G, const State<R>& S, const Consts<R>& c,
                                         R F[9]) {
+  const R sg = UNSCALED ? R(1) : G.sqrtmg;
+  const R sgp = UNSCALED ? G.ialp : G.sqrtg;  // scale of Psi
   const R wt = S.w + S.b2, pt = S.p + R(0.5) * S.b2;
   const R ud = sel<D>(S.ux, S.uy, S.uz);
   const R bd = sel<D>(S.bx, S.by, S.bz);
   const R a = wt * ud;
-  F[U_D] = G.sqrtmg * S.rho * ud;
-  F[U_TT] = G.sqrtmg * (a * S.l_t - bd * S.b_t);
-  F[U_TX] = G.sqrtmg * (a * S.lx - bd * S.b_x + (D == 0 ? pt : R(0)));
-  F[U_TY] = G.sqrtmg * (a * S.ly - bd * S.b_y + (D == 1 ? pt : R(0)));
-  F[U_TZ] = G.sqrtmg * (a * S.lz - bd * S.b_z + (D == 2 ? pt : R(0)));
+  F[U_D] = sg * S.rho * ud;
+  F[U_TT] = sg * (a * S.l_t - bd * S.b_t);
+  F[U_TX] = sg * (a * S.lx - bd * S.b_x + (D == 0 ? pt : R(0)));
+  F[U_TY] = sg * (a * S.ly - bd * S.b_y + (D == 1 ? pt : R(0)));
+  F[U_TZ] = sg * (a * S.lz - bd * S.b_z + (D == 2 ? pt : R(0)));
   const R Bd = sel<D>(S.Bx, S.By, S.Bz);
-  const R f = G.sqrtmg * S.iut;
+  const R f = sg * S.iut;
   F[U_BX] = D == 0 ? R(0) : f * (S.Bx * ud - Bd * S.ux);
   F[U_BY] = D == 1 ? R(0) : f * (S.By * ud - Bd * S.uy);
   F[U_BZ] = D == 2 ? R(0) : f * (S.Bz * ud - Bd * S.uz);
   if (CLEAN) {
-    const R gp = G.sqrtmg * S.psi;
+    const R gp = sg * S.psi;
     if constexpr (DIAG) {
       if (D == 0) F[U_BX] += gp * G.ixx;
       if (D == 1) F[U_BY] += gp * G.iyy;
       if (D == 2) F[U_BZ] += gp * G.izz;
-      F[U_PSI] = G.sqrtg * (c.ch2 * G.alp * G.alp * Bd);
+      F[U_PSI] = sgp * (c.ch2 * G.alp * G.alp * Bd);
     } else {
       F[U_BX] += gp * sel<D>(G.ixx, G.ixy, G.ixz);
       F[U_BY] += gp * sel<D>(G.ixy, G.iyy, G.iyz);
       F[U_BZ] += gp * sel<D>(G.ixz, G.iyz, G.izz);
-      F[U_PSI] = G.sqrtg * (c.ch2 * G.alp * G.alp * Bd - sel<D>(G.bx, G.by, G.bz) * S.psi);
+      F[U_PSI] = sgp * (c.ch2 * G.alp * G.alp * Bd - sel<D>(G.bx, G.by, G.bz) * S.psi);
     }
   }
 }
