@@ -38,7 +38,7 @@
 #include "hzn_ctx.h"
 #include "hzn_internal.h"
 #include "hzn_physics.cuh"
-#include "hzn_adjoint.cuh"
+#include "hzn_adj.h"
 
 namespace hzn {
 namespace {
@@ -148,10 +148,12 @@ void launch_cell(hz_adjoint* a, const void* Pb, int stage, int gather) {
   const long long n = (long long)c->g.n[0] * c->g.n[1] * c->g.n[2];
   const int threads = block_threads(n);
   const int blocks = grid_blocks(n, threads);
-  if (c->o.cleaning)
-    k_adj_cell<true><<<blocks, threads, 0, c->st>>>(c->kp, sh, (const double*)Pb, (const double*)c->met, a->bufs);
+  if (c->v.diag)
+    adj_launch_cell<true>(c->o.cleaning, blocks, threads, c->st, c->kp, sh, (const double*)Pb,
+                          (const double*)c->met, a->bufs);
   else
-    k_adj_cell<false><<<blocks, threads, 0, c->st>>>(c->kp, sh, (const double*)Pb, (const double*)c->met, a->bufs);
+    adj_launch_cell<false>(c->o.cleaning, blocks, threads, c->st, c->kp, sh, (const double*)Pb,
+                           (const double*)c->met, a->bufs);
 }
 
 void launch_face(hz_adjoint* a, const void* Ps) {
@@ -168,10 +170,12 @@ void launch_face(hz_adjoint* a, const void* Ps) {
   }
   const int threads = block_threads(nmax);
   dim3 grid(grid_blocks(nmax, threads), a->A.ndir);
-  if (c->o.cleaning)
-    k_adj_face<true><<<grid, threads, 0, c->st>>>(c->kp, sh, (const double*)Ps, (const double*)c->met, a->bufs);
+  if (c->v.diag)
+    adj_launch_face<true>(c->o.cleaning, grid, threads, c->st, c->kp, sh, (const double*)Ps,
+                          (const double*)c->met, a->bufs);
   else
-    k_adj_face<false><<<grid, threads, 0, c->st>>>(c->kp, sh, (const double*)Ps, (const double*)c->met, a->bufs);
+    adj_launch_face<false>(c->o.cleaning, grid, threads, c->st, c->kp, sh, (const double*)Ps,
+                           (const double*)c->met, a->bufs);
 }
 
 }  // namespace

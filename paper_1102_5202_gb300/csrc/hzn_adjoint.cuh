@@ -6,9 +6,12 @@
 // source, and the implicit-function adjoint of the primitive recovery (§2.2).  The metric is
 // held fixed (it is not differentiated).  Every function computes a vector-Jacobian product:
 // given the adjoint ("bar") of its outputs it adds the adjoint of its inputs.  The two kernels
-// of a reverse substep (k_adj_face, k_adj_cell) close the file; hzn_adjoint.cu launches them.
+// of a reverse substep (k_adj_face, k_adj_cell) and their host launchers close the file; each
+// metric class (diagonal, general) is instantiated in its own unit (hzn_adj_diag.cu,
+// hzn_adj_general.cu).
 #pragma once
 
+#include "hzn_adj.h"
 #include "hzn_internal.h"
 #include "hzn_physics.cuh"
 
@@ -50,9 +53,11 @@ __device__ __forceinline__ double& selr(double& x, double& y, double& z) {
   return D == 0 ? x : (D == 1 ? y : z);
 }
 
-// Reverse of make_state (general 3+1 metric, metric held fixed): adds dJ/dP to Pb.
-__device__ void state_rev(const Geom<double>& G, const State<double>& S, const double P[9],
-                          double gfac, SBar& s, double Pb[9]) {
+// Reverse of make_state (metric held fixed): adds dJ/dP to Pb.  DIAG: zero shift and diagonal
+// gamma_ij, whose identically zero terms are dropped (as make_state<true> drops them).
+template <bool DIAG>
+__device__ __forceinline__ void state_rev(const Geom<double>& G, const State<double>& S,
+                                          const double P[9], double gfac, SBar& s, double Pb[9]) {
   // b^2 = b^t b_t + b^i b_i
   s.bt += s.b2 * S.b_t;
   s.b_t += s.b2 * S.bt;
@@ -62,16 +67,21 @@ __device__ void state_rev(const Geom<double>& G, const State<double>& S, const d
   s.b_x += s.b2 * S.bx;
   s.b_y += s.b2 * S.by;
   s.b_z += s.b2 * S.bz;
-  // b_t = g_tt b^t + beta_i b^i
+  // b_t = g_tt b^t + beta_i b^i ; b_i = beta_i b^t + gamma_ij b^j
   s.bt += G.gtt * s.b_t;
-  s.bx += G.blx * s.b_t;
-  s.by += G.bly * s.b_t;
-  s.bz += G.blz * s.b_t;
-  // b_i = beta_i b^t + gamma_ij b^j
-  s.bt += G.blx * s.b_x + G.bly * s.b_y + G.blz * s.b_z;
-  s.bx += G.gxx * s.b_x + G.gxy * s.b_y + G.gxz * s.b_z;
-  s.by += G.gxy * s.b_x + G.gyy * s.b_y + G.gyz * s.b_z;
-  s.bz += G.gxz * s.b_x + G.gyz * s.b_y + G.gzz * s.b_z;
+  if constexpr (DIAG) {
+    s.bx += G.gxx * s.b_x;
+    s.by += G.gyy * s.b_y;
+    s.bz += G.gzz * s.b_z;
+  } else {
+    s.bx += G.blx * s.b_t;
+    s.by += G.bly * s.b_t;
+    s.bz += G.blz * s.b_t;
+    s.bt += G.blx * s.b_x + G.bly * s.b_y + G.blz * s.b_z;
+    s.bx += G.gxx * s.b_x + G.gxy * s.b_y + G.gxz * s.b_z;
+    s.by += G.gxy * s.b_x + G.gyy * s.b_y + G.gyz * s.b_z;
+    s.bz += G.gxz * s.b_x + G.gyz * s.b_y + G.gzz * s.b_z;
+  }
   // b^i = (B^i + b^t u^i) / u^t ; B^i + b^t u^i = b^i u^t
   s.Bx += S.iut * s.bx;
   s.By += S.iut * s.by;
@@ -92,12 +102,14 @@ __device__ void state_rev(const Geom<double>& G, const State<double>& S, const d
   Pb[P_UX] += s.ux;
   Pb[P_UY] += s.uy;
   Pb[P_UZ] += s.uz;
-  s.ut -= G.bx * s.ux + G.by * s.uy + G.bz * s.uz;
   // u_t = -alpha W + beta^i u_i
   s.W -= G.alp * s.l_t;
-  s.lx += G.bx * s.l_t;
-  s.ly += G.by * s.l_t;
-  s.lz += G.bz * s.l_t;
+  if constexpr (!DIAG) {
+    s.ut -= G.bx * s.ux + G.by * s.uy + G.bz * s.uz;
+    s.lx += G.bx * s.l_t;
+    s.ly += G.by * s.l_t;
+    s.lz += G.bz * s.l_t;
+  }
   // u^t = W / alpha, 1/u^t = alpha / W
   s.W += s.ut * G.ialp - s.iut * S.iut / S.W;
   // W = sqrt(q), q = 1 + u_i u~^i
@@ -109,9 +121,15 @@ __device__ void state_rev(const Geom<double>& G, const State<double>& S, const d
   Pb[P_UY] += S.ly * qb;
   Pb[P_UZ] += S.lz * qb;
   // u_i = gamma_ij u~^j
-  Pb[P_UX] += G.gxx * s.lx + G.gxy * s.ly + G.gxz * s.lz;
-  Pb[P_UY] += G.gxy * s.lx + G.gyy * s.ly + G.gyz * s.lz;
-  Pb[P_UZ] += G.gxz * s.lx + G.gyz * s.ly + G.gzz * s.lz;
+  if constexpr (DIAG) {
+    Pb[P_UX] += G.gxx * s.lx;
+    Pb[P_UY] += G.gyy * s.ly;
+    Pb[P_UZ] += G.gzz * s.lz;
+  } else {
+    Pb[P_UX] += G.gxx * s.lx + G.gxy * s.ly + G.gxz * s.lz;
+    Pb[P_UY] += G.gxy * s.lx + G.gyy * s.ly + G.gyz * s.lz;
+    Pb[P_UZ] += G.gxz * s.lx + G.gyz * s.ly + G.gzz * s.lz;
+  }
   // w = rho + gamma/(gamma-1) p
   Pb[P_RHO] += s.rho + s.w;
   Pb[P_PRS] += s.p + gfac * s.w;
@@ -155,7 +173,7 @@ __device__ __forceinline__ void cons_rev(const Geom<double>& G, const State<doub
 }
 
 // Reverse of flux_of along D: flux adjoint Fb into the state bars.
-template <int D, bool CLEAN>
+template <int D, bool CLEAN, bool DIAG>
 __device__ __forceinline__ void flux_rev(const Geom<double>& G, const State<double>& S,
                                          const Consts<double>& c, const double Fb[9], SBar& s) {
   const double sg = G.sqrtmg;
@@ -199,9 +217,13 @@ __device__ __forceinline__ void flux_rev(const Geom<double>& G, const State<doub
   s.uz -= gz * ti * Bd;
   if (CLEAN) {
     // sqrt(-g) gamma^{Dj} psi on B^j; sqrt(gamma)(c_h^2 alpha^2 B^D - beta^D psi) on Psi
-    s.psi += sg * (sel<D>(G.ixx, G.ixy, G.ixz) * Fb[U_BX] + sel<D>(G.ixy, G.iyy, G.iyz) * Fb[U_BY] +
-                   sel<D>(G.ixz, G.iyz, G.izz) * Fb[U_BZ]) -
-             G.sqrtg * sel<D>(G.bx, G.by, G.bz) * Fb[U_PSI];
+    if constexpr (DIAG) {
+      s.psi += sg * sel<D>(G.ixx, G.iyy, G.izz) * Fb[U_BX + D];
+    } else {
+      s.psi += sg * (sel<D>(G.ixx, G.ixy, G.ixz) * Fb[U_BX] + sel<D>(G.ixy, G.iyy, G.iyz) * Fb[U_BY] +
+                     sel<D>(G.ixz, G.iyz, G.izz) * Fb[U_BZ]) -
+               G.sqrtg * sel<D>(G.bx, G.by, G.bz) * Fb[U_PSI];
+    }
     Bdb += G.sqrtg * c.ch2 * G.alp * G.alp * Fb[U_PSI];
   }
   selr<D>(s.ux, s.uy, s.uz) += udb;
@@ -213,7 +235,7 @@ __device__ __forceinline__ void flux_rev(const Geom<double>& G, const State<doub
 }
 
 // Reverse of cms2_of + speeds_of along D: adjoints lmb, lpb of the two roots into the bars.
-template <int D>
+template <int D, bool DIAG>
 __device__ __forceinline__ void speeds_rev(const Geom<double>& G, const State<double>& S,
                                            const Consts<double>& c, double lmb, double lpb,
                                            SBar& s) {
@@ -225,9 +247,9 @@ __device__ __forceinline__ void speeds_rev(const Geom<double>& G, const State<do
   const double ia2 = G.ialp * G.ialp;
   const double ud = sel<D>(S.ux, S.uy, S.uz);
   const double oc = 1.0 - c2;
-  const double bd = sel<D>(G.bx, G.by, G.bz);
-  const double gtd = bd * ia2;
-  const double gdd = sel<D>(G.ixx, G.iyy, G.izz) - bd * bd * ia2;
+  const double bd = DIAG ? 0.0 : sel<D>(G.bx, G.by, G.bz);
+  const double gtd = DIAG ? 0.0 : bd * ia2;
+  const double gdd = DIAG ? sel<D>(G.ixx, G.iyy, G.izz) : sel<D>(G.ixx, G.iyy, G.izz) - bd * bd * ia2;
   const double A = oc * S.ut * S.ut + c2 * ia2;
   const double B = -2.0 * (oc * S.ut * ud - c2 * gtd);
   const double C = oc * ud * ud - c2 * gdd;
@@ -275,7 +297,7 @@ __device__ __forceinline__ void mc_coef(double dm, double dp, double& cm, double
 
 // Face reverse along D at the face i - 1/2 of cell (i, j, k): recompute the face state, then
 // push the face-flux adjoint Fb back to the reconstructed left / right primitive states.
-template <int D, bool CLEAN>
+template <int D, bool CLEAN, bool DIAG>
 __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const double* __restrict__ M,
                          int i, int j, int k, const double Fb[9], double PLb[9], double PRb[9]) {
   constexpr int NV = CLEAN ? 9 : 8;
@@ -297,27 +319,31 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
     PR[f] = cc - mc_half_slope(cc - b, d - cc);
   }
   if (!CLEAN) PL[8] = PR[8] = 0.0;
-  double m[10];
-  {
-    const long long o1 = (long long)(k + kp.gz) * kp.mplane + (long long)(j + kp.gy) * kp.mpitch + (i + kp.gx);
+  const long long o1 = (long long)(k + kp.gz) * kp.mplane + (long long)(j + kp.gy) * kp.mpitch + (i + kp.gx);
+  Geom<double> G;
+  if constexpr (DIAG) {
+    // face geometry of the diagonal metric from its table
+    G = geo_load<double>(kp.geo_f + D * GEO_N * kp.ms, o1, kp.ms);
+  } else {
+    double m[10];
     const long long o0 = o1 - (D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane));
 #pragma unroll
     for (int f = 0; f < 10; ++f) m[f] = 0.5 * (M[f * kp.ms + o0] + M[f * kp.ms + o1]);
+    G = make_geom<false>(m);
   }
-  const Geom<double> G = make_geom<false>(m);
   Consts<double> c;
   c.gamma = kp.gamma;
   c.gfac = kp.gfac;
   c.ch = kp.ch;
   c.ch2 = kp.ch * kp.ch;
-  const State<double> SL = make_state<false>(G, PL, c), SR = make_state<false>(G, PR, c);
+  const State<double> SL = make_state<DIAG>(G, PL, c), SR = make_state<DIAG>(G, PR, c);
   double FL[9], UL[9], FR[9], UR[9], lmL, lpL, lmR, lpR;
-  flux_of<D, CLEAN, false>(G, SL, c, FL);
+  flux_of<D, CLEAN, DIAG>(G, SL, c, FL);
   cons_of<CLEAN>(G, SL, UL);
-  speeds_of<D, false>(G, SL, cms2_of(SL, c), lmL, lpL);
-  flux_of<D, CLEAN, false>(G, SR, c, FR);
+  speeds_of<D, DIAG>(G, SL, cms2_of(SL, c), lmL, lpL);
+  flux_of<D, CLEAN, DIAG>(G, SR, c, FR);
   cons_of<CLEAN>(G, SR, UR);
-  speeds_of<D, false>(G, SR, cms2_of(SR, c), lmR, lpR);
+  speeds_of<D, DIAG>(G, SR, cms2_of(SR, c), lmR, lpR);
   if (!CLEAN) FL[8] = FR[8] = UL[8] = UR[8] = 0.0;
   // frozen wave-speed bounds: sL = min(0, lmL, lmR), sR = max(0, lpL, lpR)
   const bool mr = lmR < lmL;
@@ -355,7 +381,7 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
   if (CLEAN) {
     // the pair (B^D, Psi) with the metric-only cleaning speeds
     double cm, cp;
-    clean_speeds<D, false>(G, c.ch, cm, cp);
+    clean_speeds<D, DIAG>(G, c.ch, cm, cp);
     const double csl = fmin(0.0, cm), csr = fmax(0.0, cp);
     const double cden = csr - csl;
     const double ic = 1.0 / cden;
@@ -376,25 +402,25 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
   {
     SBar s;
     zero(s);
-    flux_rev<D, CLEAN>(G, SL, c, FLb, s);
+    flux_rev<D, CLEAN, DIAG>(G, SL, c, FLb, s);
     cons_rev<CLEAN>(G, SL, ULb, s);
-    speeds_rev<D>(G, SL, c, lmLb, lpLb, s);
-    state_rev(G, SL, PL, c.gfac, s, PLb);
+    speeds_rev<D, DIAG>(G, SL, c, lmLb, lpLb, s);
+    state_rev<DIAG>(G, SL, PL, c.gfac, s, PLb);
   }
   {
     SBar s;
     zero(s);
-    flux_rev<D, CLEAN>(G, SR, c, FRb, s);
+    flux_rev<D, CLEAN, DIAG>(G, SR, c, FRb, s);
     cons_rev<CLEAN>(G, SR, URb, s);
-    speeds_rev<D>(G, SR, c, lmRb, lpRb, s);
-    state_rev(G, SR, PR, c.gfac, s, PRb);
+    speeds_rev<D, DIAG>(G, SR, c, lmRb, lpRb, s);
+    state_rev<DIAG>(G, SR, PR, c.gfac, s, PRb);
   }
   if (!CLEAN) PLb[8] = PRb[8] = 0.0;
 }
 
 // Reverse of the metric source 1/2 sqrt(-g) T^{ab} d_i g_ab (centred differences) and of the
 // cleaning damping -kappa alpha sqrt(gamma) psi at one cell, given lam_L there.
-template <bool CLEAN>
+template <bool CLEAN, bool DIAG>
 __device__ void source_rev(const KParams& kp, const double* __restrict__ M, long long mo,
                            const Geom<double>& G, const State<double>& S, const double Pc[9],
                            const double Lb[9], const Consts<double>& c, double Pb[9]) {
@@ -411,6 +437,17 @@ __device__ void source_rev(const KParams& kp, const double* __restrict__ M, long
     if (!act) continue;
     const double wgt = Lb[U_TX + d] * h * 0.5 * (d == 0 ? kp.idx : (d == 1 ? kp.idy : kp.idz));
     if (wgt == 0.0) continue;
+    if constexpr (DIAG) {
+      // tabulated differences of g_tt, g_xx, g_yy, g_zz (the only nonzero components)
+      const double* g = kp.geo_s + d * GEO_S * kp.ms + mo;
+      const double dtt = g[0], dxx = g[kp.ms], dyy = g[2 * kp.ms], dzz = g[3 * kp.ms];
+      if (dtt != 0.0 || dxx != 0.0 || dyy != 0.0 || dzz != 0.0) any = true;
+      Mb[0] += wgt * dtt;
+      Mb[4] += wgt * dxx;
+      Mb[7] += wgt * dyy;
+      Mb[9] += wgt * dzz;
+      continue;
+    }
     const long long st = d == 0 ? 1 : (d == 1 ? kp.mpitch : kp.mplane);
     double gp[10], gm[10];
 #pragma unroll
@@ -452,14 +489,27 @@ __device__ void source_rev(const KParams& kp, const double* __restrict__ M, long
   const double ia2 = G.ialp * G.ialp;
   const double u4[4] = {S.ut, S.ux, S.uy, S.uz};
   const double b4[4] = {S.bt, S.bx, S.by, S.bz};
+  const double wt = S.w + S.b2;
+  double wtb = 0.0, ptb = 0.0, u4b[4] = {0, 0, 0, 0}, b4b[4] = {0, 0, 0, 0};
+  if constexpr (DIAG) {
+    // diagonal components tt, xx, yy, zz only
+    const double gi[4] = {-ia2, G.ixx, G.iyy, G.izz};
+    const int qd[4] = {0, 4, 7, 9};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const double t = Mb[qd[a]];
+      wtb += t * u4[a] * u4[a];
+      ptb += t * gi[a];
+      u4b[a] += 2.0 * t * wt * u4[a];
+      b4b[a] -= 2.0 * t * b4[a];
+    }
+  } else {
   const double gi[10] = {-ia2, G.bx * ia2, G.by * ia2, G.bz * ia2,
                          G.ixx - G.bx * G.bx * ia2, G.ixy - G.bx * G.by * ia2,
                          G.ixz - G.bx * G.bz * ia2, G.iyy - G.by * G.by * ia2,
                          G.iyz - G.by * G.bz * ia2, G.izz - G.bz * G.bz * ia2};
   const int ia[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
   const int ib[10] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
-  const double wt = S.w + S.b2;
-  double wtb = 0.0, ptb = 0.0, u4b[4] = {0, 0, 0, 0}, b4b[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
     const double t = Mb[q];
@@ -470,6 +520,7 @@ __device__ void source_rev(const KParams& kp, const double* __restrict__ M, long
     u4b[b] += t * wt * u4[a];
     b4b[a] -= t * b4[b];
     b4b[b] -= t * b4[a];
+  }
   }
   SBar s;
   zero(s);
@@ -484,18 +535,18 @@ __device__ void source_rev(const KParams& kp, const double* __restrict__ M, long
   s.bx += b4b[1];
   s.by += b4b[2];
   s.bz += b4b[3];
-  state_rev(G, S, Pc, c.gfac, s, Pb);
+  state_rev<DIAG>(G, S, Pc, c.gfac, s, Pb);
 }
 
 // (dU/dP)^T v at one state: the conserved-vector adjoint v pushed back to the primitives.
-template <bool CLEAN>
+template <bool CLEAN, bool DIAG>
 __device__ __forceinline__ void cons_vjp(const Geom<double>& G, const State<double>& S,
                                          const double Pc[9], const Consts<double>& c,
                                          const double v[9], double out[9]) {
   SBar s;
   zero(s);
   cons_rev<CLEAN>(G, S, v, s);
-  state_rev(G, S, Pc, c.gfac, s, out);
+  state_rev<DIAG>(G, S, Pc, c.gfac, s, out);
 }
 
 // Solve A^T x = r for the 5 x 5 hydrodynamic block (partial pivoting).  At[m][k] = dU_k/dP_m.
@@ -540,7 +591,7 @@ __device__ __forceinline__ void solve5(double At[5][5], double r[5]) {
 }
 
 // mu = (dU/dP)^{-T} lamP at the state (implicit-function adjoint of the recovery).
-template <bool CLEAN>
+template <bool CLEAN, bool DIAG>
 __device__ void ift(const Geom<double>& G, const State<double>& S, const double Pc[9],
                     const Consts<double>& c, const double lamP[9], double mu[9]) {
   // rows k of dU/dP for the hydrodynamic components D, T_t, T_x, T_y, T_z
@@ -550,7 +601,7 @@ __device__ void ift(const Geom<double>& G, const State<double>& S, const double 
     double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     e[kq] = 1.0;
     double row[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    cons_vjp<CLEAN>(G, S, Pc, c, e, row);
+    cons_vjp<CLEAN, DIAG>(G, S, Pc, c, e, row);
 #pragma unroll
     for (int m = 0; m < 5; ++m) At[m][kq] = row[m];
 #pragma unroll
@@ -571,30 +622,9 @@ __device__ void ift(const Geom<double>& G, const State<double>& S, const double 
   mu[8] = CLEAN ? lamP[8] / G.sqrtg : 0.0;
 }
 
-// Shapes of the adjoint arrays.  Cell arrays use the forward layout (kp.pitch, kp.plane,
-// kp.fs); face arrays hold faces i - 1/2 for i = 0 .. n_D along D, one more cell per axis.
-struct AdjShape {
-  int fpitch;
-  long long fplane, ffs;
-  double dt;
-  double a, b;     // stage coefficients of the substep whose implicit-function step runs
-  int stage;       // 0, 1, 2 for that substep; 3: final (adjoint of the initial primitives)
-  int gather;      // 1: gather lam_P from the faces of the later substep; 0: read lam_P
-};
-
-struct AdjBufs {
-  double* lamP;    // adjoint of the primitive state at the current substep boundary
-  double* lamU;    // adjoint of the conserved state there
-  double* lamA;    // accumulated adjoint of the step's starting conserved state U0
-  double* lamL;    // b dt mu of the substep being reversed (adjoint of L)
-  double* fL[3];   // per axis: adjoint of the left reconstructed state, 9 fields
-  double* fR[3];   // per axis: adjoint of the right reconstructed state
-  double* out;     // final: adjoint of the initial primitives (padded layout)
-};
-
 // One thread per face of every active axis: flux adjoint from lam_L, face reverse, store the
 // adjoints of the two reconstructed states.
-template <bool CLEAN>
+template <bool CLEAN, bool DIAG>
 __global__ void __launch_bounds__(128) k_adj_face(const KParams kp, const AdjShape sh,
                                                   const double* __restrict__ P,
                                                   const double* __restrict__ M, AdjBufs bufs) {
@@ -619,9 +649,9 @@ __global__ void __launch_bounds__(128) k_adj_face(const KParams kp, const AdjSha
       Fb[f] = (r - l) * idd;
     }
     double PLb[9], PRb[9];
-    if (D == 0) face_rev<0, CLEAN>(kp, P, M, i, j, k, Fb, PLb, PRb);
-    else if (D == 1) face_rev<1, CLEAN>(kp, P, M, i, j, k, Fb, PLb, PRb);
-    else face_rev<2, CLEAN>(kp, P, M, i, j, k, Fb, PLb, PRb);
+    if (D == 0) face_rev<0, CLEAN, DIAG>(kp, P, M, i, j, k, Fb, PLb, PRb);
+    else if (D == 1) face_rev<1, CLEAN, DIAG>(kp, P, M, i, j, k, Fb, PLb, PRb);
+    else face_rev<2, CLEAN, DIAG>(kp, P, M, i, j, k, Fb, PLb, PRb);
     const long long fo = (long long)k * sh.fplane + (long long)j * sh.fpitch + i;
     double* fl = bufs.fL[D];
     double* fr = bufs.fR[D];
@@ -720,7 +750,7 @@ __device__ __forceinline__ void gather_axis(const KParams& kp, const AdjShape& s
 // One thread per cell: (1) lam_P at the boundary state Pb -- gathered from the faces of the
 // later substep plus its source reverse, or read from lamP; (2) the implicit-function step of
 // the earlier substep (or, at the initial state, the adjoint of the initial primitives).
-template <bool CLEAN>
+template <bool CLEAN, bool DIAG>
 __global__ void __launch_bounds__(128) k_adj_cell(const KParams kp, const AdjShape sh,
                                                   const double* __restrict__ Pb,
                                                   const double* __restrict__ M, AdjBufs bufs) {
@@ -738,13 +768,19 @@ __global__ void __launch_bounds__(128) k_adj_cell(const KParams kp, const AdjSha
     const int k = (int)(q / ((long long)kp.nx * kp.ny));
     const long long off = (long long)k * kp.plane + (long long)j * kp.pitch + i;
     const long long mo = (long long)(k + kp.gz) * kp.mplane + (long long)(j + kp.gy) * kp.mpitch + (i + kp.gx);
-    double Pc[9], m[10];
+    double Pc[9];
 #pragma unroll
     for (int f = 0; f < 9; ++f) Pc[f] = f < NV ? Pb[f * kp.fs + off] : 0.0;
+    Geom<double> G;
+    if constexpr (DIAG) {
+      G = geo_load<double>(kp.geo_c, mo, kp.ms);
+    } else {
+      double m[10];
 #pragma unroll
-    for (int f = 0; f < 10; ++f) m[f] = M[f * kp.ms + mo];
-    const Geom<double> G = make_geom<false>(m);
-    const State<double> S = make_state<false>(G, Pc, c);
+      for (int f = 0; f < 10; ++f) m[f] = M[f * kp.ms + mo];
+      G = make_geom<false>(m);
+    }
+    const State<double> S = make_state<DIAG>(G, Pc, c);
     double lamP[9];
     if (sh.gather) {
 #pragma unroll
@@ -755,7 +791,7 @@ __global__ void __launch_bounds__(128) k_adj_cell(const KParams kp, const AdjSha
       double Lb[9];
 #pragma unroll
       for (int f = 0; f < 9; ++f) Lb[f] = f < NV ? bufs.lamL[f * kp.fs + off] : 0.0;
-      source_rev<CLEAN>(kp, M, mo, G, S, Pc, Lb, c, lamP);
+      source_rev<CLEAN, DIAG>(kp, M, mo, G, S, Pc, Lb, c, lamP);
     } else {
 #pragma unroll
       for (int f = 0; f < 9; ++f) lamP[f] = f < NV ? bufs.lamP[f * kp.fs + off] : 0.0;
@@ -765,7 +801,7 @@ __global__ void __launch_bounds__(128) k_adj_cell(const KParams kp, const AdjSha
     for (int f = 0; f < 9; ++f) lamU[f] = f < NV ? bufs.lamU[f * kp.fs + off] : 0.0;
     if (sh.stage == 3) {
       // initial state: U(0) = w(P(0)), so lam_P(0) += (dU/dP)^T lam_U(0)
-      cons_vjp<CLEAN>(G, S, Pc, c, lamU, lamP);
+      cons_vjp<CLEAN, DIAG>(G, S, Pc, c, lamU, lamP);
 #pragma unroll
       for (int f = 0; f < NV; ++f) bufs.out[f * kp.fs + off] = lamP[f];
       continue;
@@ -780,7 +816,7 @@ __global__ void __launch_bounds__(128) k_adj_cell(const KParams kp, const AdjSha
       double tot[9];
 #pragma unroll
       for (int f = 0; f < 9; ++f) tot[f] = lamP[f];
-      cons_vjp<CLEAN>(G, S, Pc, c, lamU, tot);
+      cons_vjp<CLEAN, DIAG>(G, S, Pc, c, lamU, tot);
       if (atm) {
         // only B (and psi) of the atmosphere state depend on the conserved input
 #pragma unroll
@@ -790,10 +826,10 @@ __global__ void __launch_bounds__(128) k_adj_cell(const KParams kp, const AdjSha
         mu[8] = CLEAN ? tot[8] / G.sqrtg : 0.0;
       } else {
         tot[P_PRS] = 0.0;
-        ift<CLEAN>(G, S, Pc, c, tot, mu);
+        ift<CLEAN, DIAG>(G, S, Pc, c, tot, mu);
       }
     } else {
-      ift<CLEAN>(G, S, Pc, c, lamP, mu);
+      ift<CLEAN, DIAG>(G, S, Pc, c, lamP, mu);
 #pragma unroll
       for (int f = 0; f < 9; ++f) mu[f] += lamU[f];
     }
@@ -812,6 +848,21 @@ __global__ void __launch_bounds__(128) k_adj_cell(const KParams kp, const AdjSha
       }
     }
   }
+}
+
+// Host launchers (declared in hzn_adj.h, instantiated once per metric class).
+template <bool DIAG>
+void adj_launch_cell(bool clean, int blocks, int threads, cudaStream_t st, const KParams& kp,
+                     const AdjShape& sh, const double* Pb, const double* M, const AdjBufs& bufs) {
+  if (clean) k_adj_cell<true, DIAG><<<blocks, threads, 0, st>>>(kp, sh, Pb, M, bufs);
+  else k_adj_cell<false, DIAG><<<blocks, threads, 0, st>>>(kp, sh, Pb, M, bufs);
+}
+
+template <bool DIAG>
+void adj_launch_face(bool clean, dim3 grid, int threads, cudaStream_t st, const KParams& kp,
+                     const AdjShape& sh, const double* P, const double* M, const AdjBufs& bufs) {
+  if (clean) k_adj_face<true, DIAG><<<grid, threads, 0, st>>>(kp, sh, P, M, bufs);
+  else k_adj_face<false, DIAG><<<grid, threads, 0, st>>>(kp, sh, P, M, bufs);
 }
 
 }  // namespace adj

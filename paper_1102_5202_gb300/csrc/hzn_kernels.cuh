@@ -78,44 +78,6 @@ __device__ __forceinline__ void load_metric(const KParams& kp, const S* __restri
   }
 }
 
-// Geometry of a DIAG metric from a table written by k_geo_tables (the same values make_geom
-// computes from the metric).
-template <typename R>
-__device__ __forceinline__ Geom<R> geo_load(const double* __restrict__ g, long long off, long long ms) {
-  Geom<R> G;
-  G.alp = (R)__ldg(g + off);
-  G.ialp = (R)__ldg(g + ms + off);
-  G.gxx = (R)__ldg(g + 2 * ms + off);
-  G.gyy = (R)__ldg(g + 3 * ms + off);
-  G.gzz = (R)__ldg(g + 4 * ms + off);
-  G.ixx = (R)__ldg(g + 5 * ms + off);
-  G.iyy = (R)__ldg(g + 6 * ms + off);
-  G.izz = (R)__ldg(g + 7 * ms + off);
-  G.sqrtg = (R)__ldg(g + 8 * ms + off);
-  G.sqrtmg = (R)__ldg(g + 9 * ms + off);
-  G.bx = G.by = G.bz = R(0);
-  G.blx = G.bly = G.blz = R(0);
-  G.gxy = G.gxz = G.gyz = R(0);
-  G.ixy = G.ixz = G.iyz = R(0);
-  G.gtt = -G.alp * G.alp;
-  return G;
-}
-
-template <typename R>
-__device__ __forceinline__ void geo_store(double* __restrict__ g, long long off, long long ms,
-                                          const Geom<R>& G) {
-  g[off] = G.alp;
-  g[ms + off] = G.ialp;
-  g[2 * ms + off] = G.gxx;
-  g[3 * ms + off] = G.gyy;
-  g[4 * ms + off] = G.gzz;
-  g[5 * ms + off] = G.ixx;
-  g[6 * ms + off] = G.iyy;
-  g[7 * ms + off] = G.izz;
-  g[8 * ms + off] = G.sqrtg;
-  g[9 * ms + off] = G.sqrtmg;
-}
-
 // HLLE flux of the face at i - 1/2 along D of cell (i, j, k) (the face between cells i-1 and
 // i along D), written to out[f * ostride].
 // RECON 0: TVD with the MC limiter (stencil c-2 .. c+1); 1: PPM (stencil c-3 .. c+2).

@@ -96,6 +96,44 @@ __device__ __forceinline__ Geom<R> make_geom(const R m[10]) {
   return G;
 }
 
+// Geometry of a DIAG metric from a table of GEO_N fields at stride ms (alpha, 1/alpha, gamma_xx,
+// _yy, _zz, gamma^xx, ^yy, ^zz, sqrt(gamma), sqrt(-g)): the values make_geom<true> computes.
+template <typename R>
+__device__ __forceinline__ Geom<R> geo_load(const double* __restrict__ g, long long off, long long ms) {
+  Geom<R> G;
+  G.alp = (R)__ldg(g + off);
+  G.ialp = (R)__ldg(g + ms + off);
+  G.gxx = (R)__ldg(g + 2 * ms + off);
+  G.gyy = (R)__ldg(g + 3 * ms + off);
+  G.gzz = (R)__ldg(g + 4 * ms + off);
+  G.ixx = (R)__ldg(g + 5 * ms + off);
+  G.iyy = (R)__ldg(g + 6 * ms + off);
+  G.izz = (R)__ldg(g + 7 * ms + off);
+  G.sqrtg = (R)__ldg(g + 8 * ms + off);
+  G.sqrtmg = (R)__ldg(g + 9 * ms + off);
+  G.bx = G.by = G.bz = R(0);
+  G.blx = G.bly = G.blz = R(0);
+  G.gxy = G.gxz = G.gyz = R(0);
+  G.ixy = G.ixz = G.iyz = R(0);
+  G.gtt = -G.alp * G.alp;
+  return G;
+}
+
+template <typename R>
+__device__ __forceinline__ void geo_store(double* __restrict__ g, long long off, long long ms,
+                                          const Geom<R>& G) {
+  g[off] = G.alp;
+  g[ms + off] = G.ialp;
+  g[2 * ms + off] = G.gxx;
+  g[3 * ms + off] = G.gyy;
+  g[4 * ms + off] = G.gzz;
+  g[5 * ms + off] = G.ixx;
+  g[6 * ms + off] = G.iyy;
+  g[7 * ms + off] = G.izz;
+  g[8 * ms + off] = G.sqrtg;
+  g[9 * ms + off] = G.sqrtmg;
+}
+
 template <int D, typename R>
 __device__ __forceinline__ R sel(R x, R y, R z) {
   return D == 0 ? x : (D == 1 ? y : z);
