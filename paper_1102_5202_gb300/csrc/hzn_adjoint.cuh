@@ -421,7 +421,7 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
 // Reverse of the metric source 1/2 sqrt(-g) T^{ab} d_i g_ab (centred differences) and of the
 // cleaning damping -kappa alpha sqrt(gamma) psi at one cell, given lam_L there.
 template <bool CLEAN, bool DIAG>
-__device__ void source_rev(const KParams& kp, const double* __restrict__ M, long long mo,
+__device__ __forceinline__ void source_rev(const KParams& kp, const double* __restrict__ M, long long mo,
                            const Geom<double>& G, const State<double>& S, const double Pc[9],
                            const double Lb[9], const Consts<double>& c, double Pb[9]) {
   // Mb[10] = sum_i lam_L[T_i] h (0.5/dx_i) (g(+i) - g(-i)), components tt, tx, ty, tz (beta_i),
@@ -549,64 +549,86 @@ __device__ __forceinline__ void cons_vjp(const Geom<double>& G, const State<doub
   state_rev<DIAG>(G, S, Pc, c.gfac, s, out);
 }
 
-// Solve A^T x = r for the 5 x 5 hydrodynamic block (partial pivoting).  At[m][k] = dU_k/dP_m.
-__device__ __forceinline__ void solve5(double At[5][5], double r[5]) {
+// One column of the elimination (partial pivoting) of the 5 x 5 system; COL is a template
+// argument so that every array index is known at compile time and the arrays stay in registers.
+template <int COL>
+__device__ __forceinline__ void elim5(double At[5][5], double r[5], double inv[5]) {
+  if constexpr (COL < 5) {
+    int piv = COL;
+    double best = fabs(At[COL][COL]);
 #pragma unroll
-  for (int col = 0; col < 5; ++col) {
-    int piv = col;
-    double best = fabs(At[col][col]);
-#pragma unroll
-    for (int rr = col + 1; rr < 5; ++rr)
-      if (fabs(At[rr][col]) > best) {
-        best = fabs(At[rr][col]);
+    for (int rr = COL + 1; rr < 5; ++rr)
+      if (fabs(At[rr][COL]) > best) {
+        best = fabs(At[rr][COL]);
         piv = rr;
       }
-    if (piv != col) {
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const double t = At[col][q];
-        At[col][q] = At[piv][q];
-        At[piv][q] = t;
+    for (int rr = COL + 1; rr < 5; ++rr) {
+      if (rr == piv) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          const double t = At[COL][q];
+          At[COL][q] = At[rr][q];
+          At[rr][q] = t;
+        }
+        const double t = r[COL];
+        r[COL] = r[rr];
+        r[rr] = t;
       }
-      const double t = r[col];
-      r[col] = r[piv];
-      r[piv] = t;
     }
-    const double inv = 1.0 / At[col][col];
+    inv[COL] = 1.0 / At[COL][COL];
 #pragma unroll
-    for (int rr = col + 1; rr < 5; ++rr) {
-      const double fct = At[rr][col] * inv;
+    for (int rr = COL + 1; rr < 5; ++rr) {
+      const double fct = At[rr][COL] * inv[COL];
 #pragma unroll
-      for (int q = col; q < 5; ++q) At[rr][q] -= fct * At[col][q];
-      r[rr] -= fct * r[col];
+      for (int q = COL; q < 5; ++q) At[rr][q] -= fct * At[COL][q];
+      r[rr] -= fct * r[COL];
     }
+    elim5<COL + 1>(At, r, inv);
   }
+}
+
+// Solve A^T x = r for the 5 x 5 hydrodynamic block (partial pivoting; back substitution with
+// the pivots' reciprocals).  At[m][k] = dU_k/dP_m.
+__device__ __forceinline__ void solve5(double At[5][5], double r[5]) {
+  double inv[5];
+  elim5<0>(At, r, inv);
 #pragma unroll
   for (int col = 4; col >= 0; --col) {
     double t = r[col];
 #pragma unroll
     for (int q = col + 1; q < 5; ++q) t -= At[col][q] * r[q];
-    r[col] = t / At[col][col];
+    r[col] = t * inv[col];
   }
+}
+
+// Row KQ of dU/dP (the conserved component KQ against every primitive) by one VJP with the
+// unit vector e_KQ; KQ is a template argument so that every index is known at compile time.
+template <int KQ, bool CLEAN, bool DIAG>
+__device__ __forceinline__ void jac_row(const Geom<double>& G, const State<double>& S,
+                                        const double Pc[9], const Consts<double>& c,
+                                        double At[5][5], double Cb[5][3]) {
+  double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  e[KQ] = 1.0;
+  double row[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  cons_vjp<CLEAN, DIAG>(G, S, Pc, c, e, row);
+#pragma unroll
+  for (int m = 0; m < 5; ++m) At[m][KQ] = row[m];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) Cb[KQ][q] = row[P_BX + q];
 }
 
 // mu = (dU/dP)^{-T} lamP at the state (implicit-function adjoint of the recovery).
 template <bool CLEAN, bool DIAG>
-__device__ void ift(const Geom<double>& G, const State<double>& S, const double Pc[9],
+__device__ __forceinline__ void ift(const Geom<double>& G, const State<double>& S, const double Pc[9],
                     const Consts<double>& c, const double lamP[9], double mu[9]) {
   // rows k of dU/dP for the hydrodynamic components D, T_t, T_x, T_y, T_z
   double At[5][5], Cb[5][3];
-#pragma unroll
-  for (int kq = 0; kq < 5; ++kq) {
-    double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    e[kq] = 1.0;
-    double row[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    cons_vjp<CLEAN, DIAG>(G, S, Pc, c, e, row);
-#pragma unroll
-    for (int m = 0; m < 5; ++m) At[m][kq] = row[m];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) Cb[kq][q] = row[P_BX + q];
-  }
+  jac_row<0, CLEAN, DIAG>(G, S, Pc, c, At, Cb);
+  jac_row<1, CLEAN, DIAG>(G, S, Pc, c, At, Cb);
+  jac_row<2, CLEAN, DIAG>(G, S, Pc, c, At, Cb);
+  jac_row<3, CLEAN, DIAG>(G, S, Pc, c, At, Cb);
+  jac_row<4, CLEAN, DIAG>(G, S, Pc, c, At, Cb);
   double x[5] = {lamP[0], lamP[1], lamP[2], lamP[3], lamP[4]};
   solve5(At, x);
   const double isg = 1.0 / G.sqrtmg;
@@ -653,8 +675,8 @@ __global__ void __launch_bounds__(128) k_adj_face(const KParams kp, const AdjSha
     else if (D == 1) face_rev<1, CLEAN, DIAG>(kp, P, M, i, j, k, Fb, PLb, PRb);
     else face_rev<2, CLEAN, DIAG>(kp, P, M, i, j, k, Fb, PLb, PRb);
     const long long fo = (long long)k * sh.fplane + (long long)j * sh.fpitch + i;
-    double* fl = bufs.fL[D];
-    double* fr = bufs.fR[D];
+    double* fl = D == 0 ? bufs.fL[0] : (D == 1 ? bufs.fL[1] : bufs.fL[2]);
+    double* fr = D == 0 ? bufs.fR[0] : (D == 1 ? bufs.fR[1] : bufs.fR[2]);
 #pragma unroll
     for (int f = 0; f < 9; ++f) {
       fl[f * sh.ffs + fo] = PLb[f];

@@ -365,7 +365,7 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
 }
 
 template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED, int RECON>
-__global__ void __launch_bounds__(TX * TY, MIXED ? 3 : 2)
+__global__ void __launch_bounds__(TX * TY, MIXED ? 4 : 2)
 k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* __restrict__ M,
           DevScalars* sc) {
   using R = typename Prec<MIXED>::R;
