@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-dw", action="store_true", help="skip the double-word face leg")
     ap.add_argument("--adjoint-reps", type=int, default=3, help="timed repetitions of the adjoint leg")
     ap.add_argument("--mixed-error", action="store_true",
                     help="also run 100 FP64 steps at the mixed size and state the mixed error (about a minute)")
@@ -246,6 +247,10 @@ def run_gpu(args, rank, world, local):
     if not args.no_variants:
         variants = run_variants(args, dist, local, base_zu_per_s=value)
 
+    dw = None
+    if not args.no_dw:
+        dw = run_dw(args, dist, local, base_zu_per_s=value)
+
     line = None
     if rank == 0:
         cpu = None
@@ -267,6 +272,7 @@ def run_gpu(args, rank, world, local):
             "ensemble": ensemble,
             "adjoint": adjoint,
             "variants": variants,
+            "fp64_dw_faces": dw,
             "gpu_launches": 4 * args.steps,
             "clocks": clk,
             "c2p_failures": int(st.c2p_failures),
@@ -455,6 +461,53 @@ def run_variants(args, dist, local, base_zu_per_s: float, steps: int = 5, warmup
         del s
         torch.cuda.empty_cache()
     return out
+
+
+def run_dw(args, dist, local, base_zu_per_s: float, steps: int = 10, warmup: int = 2):
+    """The benchmark blob with the double-word face path (FP64 state, update, recovery and CFL
+    maximum; faces, fluxes and sources in pair-of-FP32 arithmetic), timed like the main line,
+    and its per-field relative L1 distance from the FP64 path after the same steps."""
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+    from paper_1102_5202_gb300 import workloads as W
+
+    P = W.blob3d(args.n)
+    s = hzn.Solver.for_problem(P, precision=hzn.HZ_FP64_DW)
+    for _ in range(warmup):
+        s.step_cfl(0.5, 1e30)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s.stream):
+        a.record(s.stream)
+        for _ in range(steps):
+            s.step_cfl(0.5, 1e30)
+        b.record(s.stream)
+    b.synchronize()
+    sec = a.elapsed_time(b) * 1e-3
+    st = s.stats()
+    units, seconds = aggregate(float(P.ncell) * steps, sec, dist, device=torch.device("cuda", local))
+    dw_prim = s.primitives().cpu().numpy()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    # the FP64 path over the same steps from the same state
+    r = hzn.Solver.for_problem(P)
+    for _ in range(warmup + steps):
+        r.step_cfl(0.5, 1e30)
+    ref = r.primitives().cpu().numpy()
+    r.close()
+    del r
+    torch.cuda.empty_cache()
+    num = np.abs(dw_prim - ref).reshape(9, -1).sum(1)
+    den = np.abs(ref).reshape(9, -1).sum(1)
+    rel = {W.PRIM_FIELDS[f]: float(num[f] / den[f]) if den[f] > 0 else float(num[f]) for f in range(9)}
+    return {"workload": f"{P.name}_fp64_dw_faces", "value": units / seconds, "unit": UNIT,
+            "steps": steps, "ms_per_step": seconds / steps * 1e3,
+            "relative_to_fp64": units / seconds / base_zu_per_s,
+            "rel_l1_vs_fp64_gpu": rel, "c2p_failures": int(st.c2p_failures),
+            "dtype": "f64 state / f32x2 faces", "gpu_launches": 4 * steps}
 
 
 def world_size(dist):

@@ -50,7 +50,7 @@ enum {
 };
 
 enum { HZ_BC_OUTFLOW = 0, HZ_BC_PERIODIC = 1 };
-enum { HZ_FP64 = 0, HZ_MIXED = 1 };
+enum { HZ_FP64 = 0, HZ_MIXED = 1, HZ_FP64_DW = 2 };
 enum { HZ_RECON_MC = 0, HZ_RECON_PPM = 1 };
 enum { HZ_C2P_2D = 0, HZ_C2P_1D = 1 };
 
@@ -71,7 +71,13 @@ typedef struct {
   int precision;    /* HZ_FP64: every step in FP64.  HZ_MIXED: primitives and metric stored
                        in FP32; reconstruction, HLLE fluxes and sources in FP32 with the flux
                        divergence accumulated in FP32; the conserved state (stored in FP64),
-                       its RK update, the recovery and the CFL maximum in FP64 (§3.2, §6)  */
+                       its RK update, the recovery and the CFL maximum in FP64 (§3.2, §6).
+                       HZ_FP64_DW: FP64 storage, RK update, recovery and CFL maximum as for
+                       HZ_FP64; reconstruction, face states, HLLE fluxes, flux divergence and
+                       sources in double-word arithmetic (a value is the sum of two FP32
+                       numbers, about 48 significant bits) on the FP32 pipes.  MC
+                       reconstruction only (HZ_ERR_UNSUPPORTED with HZ_RECON_PPM); the
+                       adjoint and the ensemble take HZ_FP64 only                          */
   int cleaning;     /* 1: hyperbolic divergence cleaning with the field psi (§3.2)         */
   double ch;        /* cleaning speed as a fraction of light speed (0 < ch <= 1)          */
   double kappa;     /* cleaning damping rate (>= 0)                                       */

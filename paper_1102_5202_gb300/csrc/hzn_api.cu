@@ -151,7 +151,9 @@ int check_args(const hz_grid* g, const hz_options* o) {
   if (g->n[1] == 1 && g->n[2] > 1) return HZ_ERR_UNSUPPORTED;
   if ((long long)g->n[0] * g->n[1] * g->n[2] > (1LL << 31)) return HZ_ERR_ARG;
   if (!(o->gamma > 1.0) || o->gamma > 3.0) return HZ_ERR_ARG;
-  if (o->precision != HZ_FP64 && o->precision != HZ_MIXED) return HZ_ERR_ARG;
+  if (o->precision != HZ_FP64 && o->precision != HZ_MIXED && o->precision != HZ_FP64_DW)
+    return HZ_ERR_ARG;
+  if (o->precision == HZ_FP64_DW && o->recon != HZ_RECON_MC) return HZ_ERR_UNSUPPORTED;
   if (o->cleaning != 0 && o->cleaning != 1) return HZ_ERR_ARG;
   if (o->cleaning && (!(o->ch > 0.0) || o->ch > 1.0 || !(o->kappa >= 0.0))) return HZ_ERR_ARG;
   if (!(o->rho_floor > 0.0) || !(o->p_floor > 0.0) || !(o->atm_K >= 0.0)) return HZ_ERR_ARG;
@@ -235,6 +237,7 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   c->v.clean = opts->cleaning;
   c->v.mixed = opts->precision == HZ_MIXED;
   c->v.recon = opts->recon;
+  c->v.pair = opts->precision == HZ_FP64_DW;
   c->v.diag = 0;
 
   KParams& kp = c->kp;

@@ -25,6 +25,13 @@ HZN_DECLARE_PPM(32, 1)
 HZN_DECLARE_PPM(32, 2)
 HZN_DECLARE_PPM(32, 3)
 #undef HZN_DECLARE_PPM
+#define HZN_DECLARE_PAIR(D)                                                                        \
+  void launch_substep_k64x_##D##d(const Variant&, const KParams&, const StageArgs&, const void*,  \
+                                  DevScalars*, int, cudaStream_t);
+HZN_DECLARE_PAIR(1)
+HZN_DECLARE_PAIR(2)
+HZN_DECLARE_PAIR(3)
+#undef HZN_DECLARE_PAIR
 
 void launch_substep(const Variant& v, const KParams& kp, const StageArgs& sa, const void* M,
                     DevScalars* sc, int zchunks, cudaStream_t st) {
@@ -38,6 +45,12 @@ void launch_substep(const Variant& v, const KParams& kp, const StageArgs& sa, co
       else if (v.dims == 2) launch_substep_k64p_2d(v, kp, sa, M, sc, zchunks, st);
       else launch_substep_k64p_3d(v, kp, sa, M, sc, zchunks, st);
     }
+    return;
+  }
+  if (v.pair) {
+    if (v.dims == 1) launch_substep_k64x_1d(v, kp, sa, M, sc, zchunks, st);
+    else if (v.dims == 2) launch_substep_k64x_2d(v, kp, sa, M, sc, zchunks, st);
+    else launch_substep_k64x_3d(v, kp, sa, M, sc, zchunks, st);
     return;
   }
   if (v.mixed) {

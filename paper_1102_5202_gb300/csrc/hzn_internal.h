@@ -68,6 +68,7 @@ struct Variant {
   int diag;    // zero shift and diagonal gamma everywhere
   int mixed;   // FP32 storage of P and metric, FP32 faces/sources
   int recon;   // 0 MC, 1 PPM
+  int pair;    // FP64 state with double-word (f32x2) faces, fluxes and sources
 };
 
 // Launchers, one per (precision, dims) translation unit; dispatch in hzn_dispatch.cu.

@@ -21,6 +21,7 @@
 // indices, so no primitive ghosts are stored.
 #pragma once
 
+#include "hzn_f32x2.cuh"
 #include "hzn_internal.h"
 #include "hzn_physics.cuh"
 
@@ -39,6 +40,38 @@ struct Prec<true> {
   using S = float;
 };
 
+// Arithmetic type of the face, flux and source work: the precision's own, or double-word
+// (f32x2) over the FP64 state for the pair path.
+template <bool PAIR, bool MIXED>
+struct FaceType {
+  using R = typename Prec<MIXED>::R;
+};
+template <>
+struct FaceType<true, false> {
+  using R = f32x2;
+};
+
+template <typename A, typename B>
+struct SameType {
+  static constexpr bool value = false;
+};
+template <typename A>
+struct SameType<A, A> {
+  static constexpr bool value = true;
+};
+
+// Half MC slope in double-word arithmetic (the same definition as the FP64 and FP32 versions:
+// sign(dp) min(|dm|, |dp|, |dm + dp| / 4) for a strict common sign, else 0; the sign of a
+// normalised pair is the sign of its leading float, and the quarter is exact).
+__device__ __forceinline__ f32x2 mc_half_slope(f32x2 dm, f32x2 dp) {
+  const bool same = (dm.hi > 0.0f && dp.hi > 0.0f) || (dm.hi < 0.0f && dp.hi < 0.0f);
+  if (!same) return f32x2(0.0f, 0.0f);
+  const f32x2 s = dm + dp;
+  const f32x2 aq(fabsf(s.hi) * 0.25f, (s.hi < 0.0f ? -s.lo : s.lo) * 0.25f);
+  const f32x2 m = fmin(fmin(fabs(dm), fabs(dp)), aq);
+  return dp.hi > 0.0f ? m : -m;
+}
+
 __device__ __forceinline__ int bc_index(int q, int n, int periodic) {
   if (periodic) {
     q = q < 0 ? q + n : q;
@@ -55,10 +88,10 @@ __device__ __forceinline__ long long met_off(const KParams& kp, int i, int j, in
 template <typename R>
 __device__ __forceinline__ Consts<R> consts_of(const KParams& kp) {
   Consts<R> c;
-  c.gamma = (R)kp.gamma;
-  c.gfac = (R)kp.gfac;
-  c.ch = (R)kp.ch;
-  c.ch2 = (R)(kp.ch * kp.ch);
+  c.gamma = cvt<R>(kp.gamma);
+  c.gfac = cvt<R>(kp.gfac);
+  c.ch = cvt<R>(kp.ch);
+  c.ch2 = cvt<R>(kp.ch * kp.ch);
   return c;
 }
 
@@ -67,86 +100,75 @@ template <bool DIAG, typename R, typename S>
 __device__ __forceinline__ void load_metric(const KParams& kp, const S* __restrict__ M, long long off,
                                             R m[10]) {
   if constexpr (DIAG) {
-    m[M_ALP] = (R)__ldg(M + M_ALP * kp.ms + off);
-    m[M_GXX] = (R)__ldg(M + M_GXX * kp.ms + off);
-    m[M_GYY] = (R)__ldg(M + M_GYY * kp.ms + off);
-    m[M_GZZ] = (R)__ldg(M + M_GZZ * kp.ms + off);
+    m[M_ALP] = ldc<R>(M + M_ALP * kp.ms + off);
+    m[M_GXX] = ldc<R>(M + M_GXX * kp.ms + off);
+    m[M_GYY] = ldc<R>(M + M_GYY * kp.ms + off);
+    m[M_GZZ] = ldc<R>(M + M_GZZ * kp.ms + off);
     m[M_BX] = m[M_BY] = m[M_BZ] = m[M_GXY] = m[M_GXZ] = m[M_GYZ] = R(0);
   } else {
 #pragma unroll
-    for (int f = 0; f < 10; ++f) m[f] = (R)__ldg(M + f * kp.ms + off);
+    for (int f = 0; f < 10; ++f) m[f] = ldc<R>(M + f * kp.ms + off);
   }
 }
 
-// HLLE flux of the face at i - 1/2 along D of cell (i, j, k) (the face between cells i-1 and
-// i along D), written to out[f * ostride].
-// RECON 0: TVD with the MC limiter (stencil c-2 .. c+1); 1: PPM (stencil c-3 .. c+2).
-template <int D, bool CLEAN, bool DIAG, int RECON, typename R, typename S>
-__device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict__ P,
-                                          const S* __restrict__ M, int i, int j, int k, R* out,
-                                          int ostride) {
+// HLLE flux (§2.2) of one face from its reconstructed left / right primitive states and face
+// geometry, written to out[f * ostride].  ROLL: one copy of the state code serves both states
+// (a loop the compiler keeps rolled), which halves the code of the double-word path.
+template <int D, bool CLEAN, bool DIAG, bool ROLL, typename R>
+__device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const R PR[9],
+                                          const Consts<R>& c, R* out, int ostride) {
   constexpr int NV = CLEAN ? 9 : 8;
-  constexpr int NS = RECON ? 6 : 4;
-  long long off[NS];  // stencil cells s = -NS/2 .. NS/2 - 1 along D
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    int ii = i, jj = j, kk = k;
-    if (D == 0) ii = bc_index(i + s - NS / 2, kp.nx, kp.bcx);
-    if (D == 1) jj = bc_index(j + s - NS / 2, kp.ny, kp.bcy);
-    if (D == 2) kk = bc_index(k + s - NS / 2, kp.nz, kp.bcz);
-    off[s] = (long long)kk * kp.plane + (long long)jj * kp.pitch + ii;
-  }
-  R PL[9], PR[9];
-#pragma unroll
-  for (int f = 0; f < NV; ++f) {
-    const S* pf = P + f * kp.fs;
-    if constexpr (RECON == 0) {
-      const R a = (R)__ldg(pf + off[0]), b = (R)__ldg(pf + off[1]);
-      const R cc = (R)__ldg(pf + off[2]), d = (R)__ldg(pf + off[3]);
-      const R d0 = b - a, d1 = cc - b, d2 = d - cc;
-      PL[f] = b + mc_half_slope(d0, d1);
-      PR[f] = cc - mc_half_slope(d1, d2);
-    } else {
-      ppm_face<R>((R)__ldg(pf + off[0]), (R)__ldg(pf + off[1]), (R)__ldg(pf + off[2]),
-                  (R)__ldg(pf + off[3]), (R)__ldg(pf + off[4]), (R)__ldg(pf + off[5]), PL[f], PR[f]);
-    }
-  }
-  if (!CLEAN) PL[8] = PR[8] = R(0);
-  // face metric: mean of the two adjacent centre values (tabulated for a DIAG metric in FP64)
-  Geom<R> G;
-  if constexpr (DIAG && sizeof(R) == sizeof(double)) {
-    G = geo_load<R>(kp.geo_f + D * GEO_N * kp.ms, met_off(kp, i, j, k), kp.ms);
-  } else {
-    R m[10];
-    const long long o1 = met_off(kp, i, j, k);
-    const long long o0 = o1 - (D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane));
-    R m0[10], m1[10];
-    load_metric<DIAG>(kp, M, o0, m0);
-    load_metric<DIAG>(kp, M, o1, m1);
-#pragma unroll
-    for (int f = 0; f < 10; ++f) m[f] = R(0.5) * (m0[f] + m1[f]);
-    G = make_geom<DIAG>(m);
-  }
-  const Consts<R> c = consts_of<R>(kp);
   // wave speeds.  FP64: both states' quadratics, multiplied through by w (w + b^2), share one
-  // division 0.5 / (A'_L A'_R).  FP32 (mixed): the plain quadratic per state, since A' scales
-  // like w^2 and the product underflows FP32 in near-vacuum cells.
-  constexpr bool SHARED = sizeof(R) == sizeof(double);
+  // division 0.5 / (A'_L A'_R).  FP32 (mixed) and double-word: the plain quadratic per state,
+  // since A' scales like w^2 and the product underflows the FP32 exponent range in near-vacuum
+  // cells.
+  constexpr bool SHARED = SameType<R, double>::value && !ROLL;
   R FL[9], UL[9], AL, BL, sqL, lmL, lpL;
-  {
-    const State<R> St = make_state<DIAG>(G, PL, c);
-    flux_of<D, CLEAN, DIAG, true>(G, St, c, FL);
-    cons_of<CLEAN, true>(G, St, UL);
-    if constexpr (SHARED) speed_quadratic<D, DIAG>(G, St, c, AL, BL, sqL);
-    else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmL, lpL);
-  }
   R FR[9], UR[9], AR, BR, sqR, lmR, lpR;
-  {
-    const State<R> St = make_state<DIAG>(G, PR, c);
-    flux_of<D, CLEAN, DIAG, true>(G, St, c, FR);
-    cons_of<CLEAN, true>(G, St, UR);
-    if constexpr (SHARED) speed_quadratic<D, DIAG>(G, St, c, AR, BR, sqR);
-    else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmR, lpR);
+  if constexpr (ROLL) {
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      R Pq[9];
+#pragma unroll
+      for (int f = 0; f < 9; ++f) Pq[f] = side == 0 ? PL[f] : PR[f];
+      const State<R> St = make_state<DIAG>(G, Pq, c);
+      R F[9], U[9], lm, lp;
+      flux_of<D, CLEAN, DIAG, true>(G, St, c, F);
+      cons_of<CLEAN, true>(G, St, U);
+      speeds_of<D, DIAG>(G, St, cms2_of(St, c), lm, lp);
+      if (side == 0) {
+#pragma unroll
+        for (int f = 0; f < 9; ++f) {
+          FL[f] = F[f];
+          UL[f] = U[f];
+        }
+        lmL = lm;
+        lpL = lp;
+      } else {
+#pragma unroll
+        for (int f = 0; f < 9; ++f) {
+          FR[f] = F[f];
+          UR[f] = U[f];
+        }
+        lmR = lm;
+        lpR = lp;
+      }
+    }
+  } else {
+    {
+      const State<R> St = make_state<DIAG>(G, PL, c);
+      flux_of<D, CLEAN, DIAG, true>(G, St, c, FL);
+      cons_of<CLEAN, true>(G, St, UL);
+      if constexpr (SHARED) speed_quadratic<D, DIAG>(G, St, c, AL, BL, sqL);
+      else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmL, lpL);
+    }
+    {
+      const State<R> St = make_state<DIAG>(G, PR, c);
+      flux_of<D, CLEAN, DIAG, true>(G, St, c, FR);
+      cons_of<CLEAN, true>(G, St, UR);
+      if constexpr (SHARED) speed_quadratic<D, DIAG>(G, St, c, AR, BR, sqR);
+      else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmR, lpR);
+    }
   }
   if constexpr (SHARED) {
     const R ia = R(0.5) / (AL * AR);
@@ -185,6 +207,167 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
       out[U_PSI * ostride] = (csr * FL[U_PSI] - csl * FR[U_PSI] + csl * csr * (UR[U_PSI] - UL[U_PSI])) * ic;
     }
   }
+}
+
+
+// HLLE flux of the face at i - 1/2 along D of cell (i, j, k) (the face between cells i-1 and
+// i along D), written to out[f * ostride].
+// RECON 0: TVD with the MC limiter (stencil c-2 .. c+1); 1: PPM (stencil c-3 .. c+2).
+template <int D, bool CLEAN, bool DIAG, int RECON, typename R, typename S>
+__device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict__ P,
+                                          const S* __restrict__ M, int i, int j, int k, R* out,
+                                          int ostride) {
+  constexpr int NV = CLEAN ? 9 : 8;
+  constexpr int NS = RECON ? 6 : 4;
+  long long off[NS];  // stencil cells s = -NS/2 .. NS/2 - 1 along D
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    int ii = i, jj = j, kk = k;
+    if (D == 0) ii = bc_index(i + s - NS / 2, kp.nx, kp.bcx);
+    if (D == 1) jj = bc_index(j + s - NS / 2, kp.ny, kp.bcy);
+    if (D == 2) kk = bc_index(k + s - NS / 2, kp.nz, kp.bcz);
+    off[s] = (long long)kk * kp.plane + (long long)jj * kp.pitch + ii;
+  }
+  R PL[9], PR[9];
+#pragma unroll
+  for (int f = 0; f < NV; ++f) {
+    const S* pf = P + f * kp.fs;
+    if constexpr (RECON == 0) {
+      const R a = ldc<R>(pf + off[0]), b = ldc<R>(pf + off[1]);
+      const R cc = ldc<R>(pf + off[2]), d = ldc<R>(pf + off[3]);
+      const R d0 = b - a, d1 = cc - b, d2 = d - cc;
+      PL[f] = b + mc_half_slope(d0, d1);
+      PR[f] = cc - mc_half_slope(d1, d2);
+    } else {
+      ppm_face<R>(ldc<R>(pf + off[0]), ldc<R>(pf + off[1]), ldc<R>(pf + off[2]),
+                  ldc<R>(pf + off[3]), ldc<R>(pf + off[4]), ldc<R>(pf + off[5]), PL[f], PR[f]);
+    }
+  }
+  if (!CLEAN) PL[8] = PR[8] = R(0);
+  // face metric: mean of the two adjacent centre values (tabulated for a DIAG metric in FP64)
+  Geom<R> G;
+  if constexpr (DIAG && !SameType<R, float>::value) {
+    G = geo_load<R>(kp.geo_f + D * GEO_N * kp.ms, met_off(kp, i, j, k), kp.ms);
+  } else {
+    R m[10];
+    const long long o1 = met_off(kp, i, j, k);
+    const long long o0 = o1 - (D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane));
+    R m0[10], m1[10];
+    load_metric<DIAG>(kp, M, o0, m0);
+    load_metric<DIAG>(kp, M, o1, m1);
+#pragma unroll
+    for (int f = 0; f < 10; ++f) m[f] = R(0.5) * (m0[f] + m1[f]);
+    G = make_geom<DIAG>(m);
+  }
+  const Consts<R> c = consts_of<R>(kp);
+  hlle_face<D, CLEAN, DIAG, false>(G, PL, PR, c, out, ostride);
+}
+
+// One face of the double-word path with its direction D given at run time (one copy of the
+// face code for all three directions): the stencil runs along D, and vectors and the metric are
+// rotated cyclically (component (D + a) mod 3 becomes component a) so that the face normal is x;
+// the x-direction HLLE code forms the flux, which is rotated back.
+template <bool CLEAN, bool DIAG>
+__device__ __forceinline__ void face_flux_dw(const KParams& kp, const double* __restrict__ P,
+                                             const double* __restrict__ M, int D, int i, int j, int k,
+                                             f32x2* out, int ostride) {
+  using R = f32x2;
+  constexpr int NV = CLEAN ? 9 : 8;
+  const int c0 = D, c1 = D == 2 ? 0 : D + 1, c2 = D == 0 ? 2 : D - 1;  // rotated axes
+  const int id = D == 0 ? i : (D == 1 ? j : k);
+  const int nd = D == 0 ? kp.nx : (D == 1 ? kp.ny : kp.nz);
+  const int bcd = D == 0 ? kp.bcx : (D == 1 ? kp.bcy : kp.bcz);
+  const long long base = (long long)k * kp.plane + (long long)j * kp.pitch + i;
+  const long long step = D == 0 ? 1 : (D == 1 ? kp.pitch : kp.plane);
+  long long off[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) off[s] = base + (long long)(bc_index(id + s - 2, nd, bcd) - id) * step;
+  R PL[9], PR[9];
+#pragma unroll
+  for (int f = 0; f < NV; ++f) {
+    const double* pf = P + f * kp.fs;
+    const R a = ldc<R>(pf + off[0]), b = ldc<R>(pf + off[1]);
+    const R cc = ldc<R>(pf + off[2]), d = ldc<R>(pf + off[3]);
+    const R d0 = b - a, d1 = cc - b, d2 = d - cc;
+    PL[f] = b + mc_half_slope(d0, d1);
+    PR[f] = cc - mc_half_slope(d1, d2);
+  }
+  if (!CLEAN) PL[8] = PR[8] = R(0);
+  auto pick = [](int cmp, R x, R y, R z) { return cmp == 0 ? x : (cmp == 1 ? y : z); };
+  // rotate the velocity and field components of both states
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int o = q == 0 ? P_UX : P_BX;
+    R L0 = PL[o], L1 = PL[o + 1], L2 = PL[o + 2], R0 = PR[o], R1 = PR[o + 1], R2 = PR[o + 2];
+    PL[o] = pick(c0, L0, L1, L2);
+    PL[o + 1] = pick(c1, L0, L1, L2);
+    PL[o + 2] = pick(c2, L0, L1, L2);
+    PR[o] = pick(c0, R0, R1, R2);
+    PR[o + 1] = pick(c1, R0, R1, R2);
+    PR[o + 2] = pick(c2, R0, R1, R2);
+  }
+  // face metric in the rotated frame
+  Geom<R> G;
+  const long long mo = met_off(kp, i, j, k);
+  if constexpr (DIAG) {
+    G = geo_load<R>(kp.geo_f + D * GEO_N * kp.ms, mo, kp.ms);
+    const R g0 = G.gxx, g1 = G.gyy, g2 = G.gzz, h0 = G.ixx, h1 = G.iyy, h2 = G.izz;
+    G.gxx = pick(c0, g0, g1, g2);
+    G.gyy = pick(c1, g0, g1, g2);
+    G.gzz = pick(c2, g0, g1, g2);
+    G.ixx = pick(c0, h0, h1, h2);
+    G.iyy = pick(c1, h0, h1, h2);
+    G.izz = pick(c2, h0, h1, h2);
+  } else {
+    const long long mstep = D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane);
+    R m0[10], m1[10], m[10], r[10];
+    load_metric<false>(kp, M, mo - mstep, m0);
+    load_metric<false>(kp, M, mo, m1);
+#pragma unroll
+    for (int f = 0; f < 10; ++f) m[f] = R(0.5) * (m0[f] + m1[f]);
+    // gamma_ab as a 3 x 3 table by index, then permuted
+    const R gm[3][3] = {{m[M_GXX], m[M_GXY], m[M_GXZ]}, {m[M_GXY], m[M_GYY], m[M_GYZ]},
+                        {m[M_GXZ], m[M_GYZ], m[M_GZZ]}};
+    auto gsel = [&](int a, int b) {
+      const R* row0 = gm[0];
+      const R* row1 = gm[1];
+      const R* row2 = gm[2];
+      const R x = pick(b, row0[0], row0[1], row0[2]);
+      const R y = pick(b, row1[0], row1[1], row1[2]);
+      const R z = pick(b, row2[0], row2[1], row2[2]);
+      return pick(a, x, y, z);
+    };
+    r[M_ALP] = m[M_ALP];
+    r[M_BX] = pick(c0, m[M_BX], m[M_BY], m[M_BZ]);
+    r[M_BY] = pick(c1, m[M_BX], m[M_BY], m[M_BZ]);
+    r[M_BZ] = pick(c2, m[M_BX], m[M_BY], m[M_BZ]);
+    r[M_GXX] = gsel(c0, c0);
+    r[M_GXY] = gsel(c0, c1);
+    r[M_GXZ] = gsel(c0, c2);
+    r[M_GYY] = gsel(c1, c1);
+    r[M_GYZ] = gsel(c1, c2);
+    r[M_GZZ] = gsel(c2, c2);
+    G = make_geom<false>(r);
+  }
+  const Consts<R> c = consts_of<R>(kp);
+  R F[9];
+  hlle_face<0, CLEAN, DIAG, true>(G, PL, PR, c, F, 1);
+  // rotate back: rotated component a is original component (D + a) mod 3
+  R T[3] = {F[U_TX], F[U_TY], F[U_TZ]}, B[3] = {F[U_BX], F[U_BY], F[U_BZ]};
+  auto back = [&](int orig, const R v[3]) {
+    // the rotated index a with (D + a) mod 3 == orig
+    const int a2 = orig - D;
+    const int aa = a2 < 0 ? a2 + 3 : a2;
+    return pick(aa, v[0], v[1], v[2]);
+  };
+  F[U_TX] = back(0, T);
+  F[U_TY] = back(1, T);
+  F[U_TZ] = back(2, T);
+  F[U_BX] = back(0, B);
+  F[U_BY] = back(1, B);
+  F[U_BZ] = back(2, B);
+#pragma unroll
+  for (int f = 0; f < NV; ++f) out[f * ostride] = F[f];
 }
 
 // Centre 4-metric quantities used by the source: g_tt, beta_i, gamma_ij at one cell.
@@ -364,11 +547,17 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
   return r.ok ? 0 : 1;
 }
 
-template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED, int RECON>
+// PAIR (FP64 state only): reconstruction, face states, fluxes, HLLE, divergence and sources in
+// double-word arithmetic (f32x2, on the FP32 pipes); the RK update, the recovery and the CFL
+// maximum in FP64 as on the FP64 path.
+template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED, int RECON,
+          bool PAIR = false>
 __global__ void __launch_bounds__(TX * TY, MIXED ? 4 : 2)
 k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* __restrict__ M,
           DevScalars* sc) {
-  using R = typename Prec<MIXED>::R;
+  static_assert(!(PAIR && MIXED), "the double-word faces run over the FP64 state");
+  using R = typename FaceType<PAIR, MIXED>::R;
+  using RN = typename Prec<MIXED>::R;  // type of the recovered state
   using S = typename Prec<MIXED>::S;
   constexpr int NT = TX * TY;
   constexpr int NV = CLEAN ? 9 : 8;
@@ -385,16 +574,76 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   const double dt = sc->dt;
   const Consts<R> c = consts_of<R>(kp);
   const Consts<double> cd = consts_of<double>(kp);
+  const R ridx = cvt<R>(kp.idx), ridy = cvt<R>(kp.idy), ridz = cvt<R>(kp.idz);
+  const R rhdx = cvt<R>(0.5 * kp.idx), rhdy = cvt<R>(0.5 * kp.idy), rhdz = cvt<R>(0.5 * kp.idz);
+  const R rkappa = cvt<R>(kp.kappa);
   const S* __restrict__ P = (const S*)sa.Pin;
   S* __restrict__ Pout = (S*)sa.Pout;
 
   double vloc = 0.0;
   int nfail = 0, maxit = 0;
 
-  if (ZA && own) face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX);
+  if constexpr (!PAIR) {
+    if (ZA && own) face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX);
+  }
 
   for (int k = kz0; k < kz1; ++k) {
     // ---- faces of plane k: each face of the tile once
+    if constexpr (PAIR) {
+      // one copy of the double-word face code, run in passes: x faces, y faces, the upper z
+      // face, the tile's extra row / column, and (first plane only) the lower z face
+#pragma unroll 1
+      for (int pass = 0; pass < 5; ++pass) {
+        int D = -1, ii = i, jj = j, kk = k, os = 0;
+        R* o = nullptr;
+        if (pass == 0) {
+          if (i <= kp.nx && j < kp.ny) {
+            D = 0;
+            o = &fx[0][ty][tx];
+            os = TY * (TX + 1);
+          }
+        } else if (pass == 1) {
+          if (YA && i < kp.nx && j <= kp.ny) {
+            D = 1;
+            o = &fy[0][ty][tx];
+            os = (TY + 1) * TX;
+          }
+        } else if (pass == 2) {
+          if (ZA && own) {
+            D = 2;
+            kk = k + 1;
+            o = &fz[(k + 1) & 1][0][ty][tx];
+            os = TY * TX;
+          }
+        } else if (pass == 3) {
+          if (YA && threadIdx.x < TX) {
+            ii = i0 + threadIdx.x;
+            jj = j0 + TY;
+            if (ii < kp.nx && jj <= kp.ny) {
+              D = 1;
+              o = &fy[0][TY][threadIdx.x];
+              os = (TY + 1) * TX;
+            }
+          } else if (YA ? (threadIdx.x >= 32 && threadIdx.x < 32 + TY) : threadIdx.x < TY) {
+            const int t = YA ? threadIdx.x - 32 : threadIdx.x;
+            jj = j0 + t;
+            ii = i0 + TX;
+            if (ii <= kp.nx && jj < kp.ny) {
+              D = 0;
+              o = &fx[0][t][TX];
+              os = TY * (TX + 1);
+            }
+          }
+        } else {
+          if (ZA && own && k == kz0) {
+            D = 2;
+            o = &fz[kz0 & 1][0][ty][tx];
+            os = TY * TX;
+          }
+        }
+        if (D >= 0) face_flux_dw<CLEAN, DIAG>(kp, P, M, D, ii, jj, kk, o, os);
+      }
+    } else {
     if (i <= kp.nx && j < kp.ny) face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, i, j, k, &fx[0][ty][tx], TY * (TX + 1));
     if (YA && i < kp.nx && j <= kp.ny) face_flux<1, CLEAN, DIAG, RECON>(kp, P, M, i, j, k, &fy[0][ty][tx], (TY + 1) * TX);
     if (ZA && own) face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
@@ -414,6 +663,7 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       if (ii <= kp.nx && jj < kp.ny)
         face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x][TX], TY * (TX + 1));
     }
+    }
     __syncthreads();
 
     // ---- cell update of plane k
@@ -423,9 +673,9 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       R L[9];
 #pragma unroll
       for (int f = 0; f < NV; ++f) {
-        R v = -(fx[f][ty][tx + 1] - fx[f][ty][tx]) * (R)kp.idx;
-        if (YA) v -= (fy[f][ty + 1][tx] - fy[f][ty][tx]) * (R)kp.idy;
-        if (ZA) v -= (fz[(k + 1) & 1][f][ty][tx] - fz[k & 1][f][ty][tx]) * (R)kp.idz;
+        R v = -(fx[f][ty][tx + 1] - fx[f][ty][tx]) * ridx;
+        if (YA) v -= (fy[f][ty + 1][tx] - fy[f][ty][tx]) * ridy;
+        if (ZA) v -= (fz[(k + 1) & 1][f][ty][tx] - fz[k & 1][f][ty][tx]) * ridz;
         L[f] = v;
       }
       // metric source 1/2 sqrt(-g) T^{ab} d_i g_ab (static metric: no energy source)
@@ -439,7 +689,7 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       }
       R Pc[9];
 #pragma unroll
-      for (int f = 0; f < NV; ++f) Pc[f] = (R)__ldg(P + f * kp.fs + off);
+      for (int f = 0; f < NV; ++f) Pc[f] = ldc<R>(P + f * kp.fs + off);
       if (!CLEAN) Pc[8] = R(0);
       {
         const State<R> St = make_state<DIAG>(G, Pc, c);
@@ -453,32 +703,32 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
           for (int d = 0; d < 3; ++d) {
             if ((d == 1 && !YA) || (d == 2 && !ZA)) continue;
             const double* g = gs + d * GEO_S * ms + mo;
-            const R s = T.tt * (R)__ldg(g) + T.xx * (R)__ldg(g + ms) + T.yy * (R)__ldg(g + 2 * ms) +
-                        T.zz * (R)__ldg(g + 3 * ms);
-            L[U_TX + d] += h * s * (R)(0.5 * (d == 0 ? kp.idx : (d == 1 ? kp.idy : kp.idz)));
+            const R s = T.tt * ldc<R>(g) + T.xx * ldc<R>(g + ms) + T.yy * ldc<R>(g + 2 * ms) +
+                        T.zz * ldc<R>(g + 3 * ms);
+            L[U_TX + d] += h * s * (d == 0 ? rhdx : (d == 1 ? rhdy : rhdz));
           }
         } else {
           {
             const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + 1), gm = g4_at<DIAG, R>(kp, M, mo - 1);
-            L[U_TX] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idx);
+            L[U_TX] += h * tdg<DIAG>(T, gp, gm) * rhdx;
           }
           if (YA) {
             const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + kp.mpitch), gm = g4_at<DIAG, R>(kp, M, mo - kp.mpitch);
-            L[U_TY] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idy);
+            L[U_TY] += h * tdg<DIAG>(T, gp, gm) * rhdy;
           }
           if (ZA) {
             const G4<R> gp = g4_at<DIAG, R>(kp, M, mo + kp.mplane), gm = g4_at<DIAG, R>(kp, M, mo - kp.mplane);
-            L[U_TZ] += h * tdg<DIAG>(T, gp, gm) * (R)(0.5 * kp.idz);
+            L[U_TZ] += h * tdg<DIAG>(T, gp, gm) * rhdz;
           }
         }
-        if (CLEAN) L[U_PSI] += -(R)kp.kappa * G.alp * (G.sqrtg * St.psi);
+        if (CLEAN) L[U_PSI] += -rkappa * G.alp * (G.sqrtg * St.psi);
       }
       // Runge-Kutta stage (FP64)
       double U[9];
 #pragma unroll
       for (int f = 0; f < NV; ++f) {
         const double uk = sa.Uk[f * kp.fs + off];
-        double u = sa.ak * (uk + dt * (double)L[f]);
+        double u = sa.ak * (uk + dt * to_dbl(L[f]));
         if (sa.a0 != 0.0) u += sa.a0 * sa.U0[f * kp.fs + off];
         U[f] = u;
       }
@@ -486,8 +736,24 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       // recovery of the new primitive state (FP64 Newton; the mixed path forms its guess and
       // the FP32-stored part of its result in FP32)
       int it;
-      R Pn[9];
-      if constexpr (MIXED) {
+      RN Pn[9];
+      if constexpr (PAIR) {
+        // FP64 recovery from the stored FP64 guess, FP64 CFL maximum
+        Geom<double> Gd;
+        if constexpr (DIAG) {
+          Gd = geo_load<double>(kp.geo_c, mo, kp.ms);
+        } else {
+          double md[10];
+          load_metric<DIAG>(kp, M, mo, md);
+          Gd = make_geom<DIAG>(md);
+        }
+        double Pg[9];
+#pragma unroll
+        for (int f = 0; f < NV; ++f) Pg[f] = __ldg(P + f * kp.fs + off);
+        if (!CLEAN) Pg[8] = 0.0;
+        nfail += recover<CLEAN, DIAG>(kp, Gd, U, Pg, cd, Pn, it);
+        if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, Gd, Pn, cd));
+      } else if constexpr (MIXED) {
         Geom<double> Gd;
         if constexpr (DIAG) {
           Gd = geo_load<double>(kp.geo_c, mo, kp.ms);
@@ -497,8 +763,10 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
           Gd = make_geom<DIAG>(md);
         }
         nfail += recover<CLEAN, DIAG, true, R, R>(kp, Gd, U, Pc, cd, Pn, it);
+        if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pn, c));
       } else {
         nfail += recover<CLEAN, DIAG>(kp, G, U, Pc, cd, Pn, it);
+        if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pn, c));
       }
       maxit = max(maxit, it);
 #pragma unroll
@@ -506,7 +774,6 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         sa.Uout[f * kp.fs + off] = U[f];
         Pout[f * kp.fs + off] = (S)Pn[f];
       }
-      if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pn, c));
     }
     __syncthreads();
   }
@@ -572,7 +839,7 @@ inline int blocks_for(long long n, int threads) {
 }
 
 // Launchers for one (precision, dimensionality); dispatch on cleaning and metric class.
-template <bool YA, bool ZA, bool MIXED, int RECON>
+template <bool YA, bool ZA, bool MIXED, int RECON, bool PAIR = false>
 void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, const void* Mv,
                       DevScalars* sc, int zchunks, cudaStream_t st) {
   // 1-D: one warp of cells per block, so that a short tube spreads over many SMs (each FP64
@@ -584,11 +851,11 @@ void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, 
   const S* M = (const S*)Mv;
   dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, zchunks);
   if (v.clean) {
-    if (v.diag) k_substep<TX, TY, YA, ZA, true, true, MIXED, RECON><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
-    else k_substep<TX, TY, YA, ZA, true, false, MIXED, RECON><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    if (v.diag) k_substep<TX, TY, YA, ZA, true, true, MIXED, RECON, PAIR><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    else k_substep<TX, TY, YA, ZA, true, false, MIXED, RECON, PAIR><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
   } else {
-    if (v.diag) k_substep<TX, TY, YA, ZA, false, true, MIXED, RECON><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
-    else k_substep<TX, TY, YA, ZA, false, false, MIXED, RECON><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    if (v.diag) k_substep<TX, TY, YA, ZA, false, true, MIXED, RECON, PAIR><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    else k_substep<TX, TY, YA, ZA, false, false, MIXED, RECON, PAIR><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
   }
 }
 

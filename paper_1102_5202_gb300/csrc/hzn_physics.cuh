@@ -19,6 +19,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "hzn_f32x2.cuh"
+
 namespace hzn {
 
 // Field indices of the primitive vector, of the conserved vector and of the metric.
@@ -101,16 +103,16 @@ __device__ __forceinline__ Geom<R> make_geom(const R m[10]) {
 template <typename R>
 __device__ __forceinline__ Geom<R> geo_load(const double* __restrict__ g, long long off, long long ms) {
   Geom<R> G;
-  G.alp = (R)__ldg(g + off);
-  G.ialp = (R)__ldg(g + ms + off);
-  G.gxx = (R)__ldg(g + 2 * ms + off);
-  G.gyy = (R)__ldg(g + 3 * ms + off);
-  G.gzz = (R)__ldg(g + 4 * ms + off);
-  G.ixx = (R)__ldg(g + 5 * ms + off);
-  G.iyy = (R)__ldg(g + 6 * ms + off);
-  G.izz = (R)__ldg(g + 7 * ms + off);
-  G.sqrtg = (R)__ldg(g + 8 * ms + off);
-  G.sqrtmg = (R)__ldg(g + 9 * ms + off);
+  G.alp = ldc<R>(g + off);
+  G.ialp = ldc<R>(g + ms + off);
+  G.gxx = ldc<R>(g + 2 * ms + off);
+  G.gyy = ldc<R>(g + 3 * ms + off);
+  G.gzz = ldc<R>(g + 4 * ms + off);
+  G.ixx = ldc<R>(g + 5 * ms + off);
+  G.iyy = ldc<R>(g + 6 * ms + off);
+  G.izz = ldc<R>(g + 7 * ms + off);
+  G.sqrtg = ldc<R>(g + 8 * ms + off);
+  G.sqrtmg = ldc<R>(g + 9 * ms + off);
   G.bx = G.by = G.bz = R(0);
   G.blx = G.bly = G.blz = R(0);
   G.gxy = G.gxz = G.gyz = R(0);

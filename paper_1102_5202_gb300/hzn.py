@@ -24,7 +24,7 @@ HZ_ERR_ARG, HZ_ERR_CUDA, HZ_ERR_STATE, HZ_ERR_WORKSPACE, HZ_ERR_UNSUPPORTED = -1
 HZ_ERR_TOO_LARGE = -6
 HZ_NOALLOC_SCRATCH_BYTES = 16 << 20
 HZ_BC_OUTFLOW, HZ_BC_PERIODIC = 0, 1
-HZ_FP64, HZ_MIXED = 0, 1
+HZ_FP64, HZ_MIXED, HZ_FP64_DW = 0, 1, 2
 HZ_RECON_MC, HZ_RECON_PPM = 0, 1
 HZ_C2P_2D, HZ_C2P_1D = 0, 1
 

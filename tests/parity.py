@@ -2,6 +2,8 @@
 (CUDA) and through the FP64 oracle, and compare field by field."""
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 import oracle as O
@@ -114,3 +116,20 @@ def tile_tube(P1, axis: int, other: int = 3) -> W.Problem:
     return W.Problem(P1.name + f"_ax{axis}", n, tuple(dx), (0.0, 0.0, 0.0), tuple(bc), P1.gamma,
                      np.ascontiguousarray(prim), W.minkowski_metric(n), t_end=P1.t_end, cfl=P1.cfl,
                      cleaning=P1.cleaning, ch=P1.ch, kappa=P1.kappa)
+
+
+def general_metric(X, Y, Z):
+    """A smooth periodic general static metric: lapse, shift and non-diagonal gamma_ij."""
+    m = np.zeros((10,) + X.shape)
+    m[0] = 0.85 + 0.1 * np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y)
+    m[1] = 0.05 * np.sin(2 * math.pi * Y)
+    m[2] = -0.03 * np.cos(2 * math.pi * Z)
+    m[3] = 0.02 * np.sin(2 * math.pi * X)
+    psi4 = 1.2 + 0.1 * np.cos(2 * math.pi * Z) * np.sin(2 * math.pi * X)
+    m[4] = psi4
+    m[7] = psi4 * 1.05
+    m[9] = psi4 * 0.95
+    m[5] = 0.02 * np.cos(2 * math.pi * Z)
+    m[6] = -0.015 * np.sin(2 * math.pi * Y)
+    m[8] = 0.01 * np.cos(2 * math.pi * X)
+    return m

@@ -58,7 +58,13 @@ def test_workspace_bytes_and_argument_checks(lib):
         (g, hzn.make_options(2.0, cleaning=True, ch=0.0), hzn.HZ_ERR_ARG),
         (g, hzn.make_options(2.0, c2p_maxit=0), hzn.HZ_ERR_ARG),
         (g, hzn.make_options(2.0, rho_floor=0.0), hzn.HZ_ERR_ARG),
+        (g, hzn.make_options(2.0, precision=3), hzn.HZ_ERR_ARG),
+        # the double-word face path has MC reconstruction only
+        (g, hzn.make_options(2.0, precision=hzn.HZ_FP64_DW, recon=hzn.HZ_RECON_PPM), hzn.HZ_ERR_UNSUPPORTED),
     ]
+    # the double-word face path keeps the FP64 layout
+    assert hzn.hz_workspace_bytes(g, hzn.make_options(2.0, cleaning=True, ch=0.5, kappa=1.0,
+                                                      precision=hzn.HZ_FP64_DW)) == nb
     for gg, oo, code in bad:
         n = ctypes.c_size_t(0)
         assert lib.hz_workspace_bytes(ctypes.byref(gg), ctypes.byref(oo), ctypes.byref(n)) == code

@@ -125,10 +125,10 @@ def test_tube_per_cell_density_gradient_elementwise():
 
 
 def test_general_metric_cleaning_2d_periodic():
-    from test_gpu_parity import _general_metric
+    from parity import general_metric
 
     P = W.smooth_periodic((14, 10, 1), seed=5, amp=0.2, magnetised=True)
-    P = W.with_periodic_metric(P, _general_metric)
+    P = W.with_periodic_metric(P, general_metric)
     P.cleaning, P.ch, P.kappa = True, 0.6, 0.7
     P.prim = P.prim.copy()
     P.prim[8] = 0.01 * np.random.default_rng(4).standard_normal(P.prim[8].shape)

@@ -81,10 +81,10 @@ def test_mixed_blob_one_and_five_steps():
 
 
 def test_mixed_general_metric_periodic():
-    from test_gpu_parity import _general_metric
+    from parity import general_metric
 
     P = W.smooth_periodic((37, 11, 7), seed=5, amp=0.2, magnetised=True)
-    P = W.with_periodic_metric(P, _general_metric)
+    P = W.with_periodic_metric(P, general_metric)
     P.cleaning, P.ch, P.kappa = True, 0.6, 0.7
     dt = _dt(P, 0.4)
     gp, _, gs = gpu_run(P, nsteps=2, dt=dt, solver=_mixed(P))

@@ -1,13 +1,11 @@
 """GPU parity: the CUDA path through the C-ABI against the FP64 oracle on identical seeded
 inputs.  Bar (FP64): relative L1 per field <= 1e-10 after one step and <= 1e-8 at end time."""
-import math
-
 import numpy as np
 import pytest
 
 import oracle as O
-from parity import (TOL_END, TOL_ONE_STEP, assert_parity, gpu_run, gpu_solver, oracle_run,
-                    oracle_setup, rel_l1, tile_tube)
+from parity import (TOL_END, TOL_ONE_STEP, assert_parity, general_metric, gpu_run, gpu_solver,
+                    oracle_run, oracle_setup, rel_l1, tile_tube)
 from paper_1102_5202_gb300 import hzn
 from paper_1102_5202_gb300 import workloads as W
 
@@ -82,29 +80,13 @@ def test_tube_along_each_axis(axis):
 
 
 # ------------------------------------------------------------------ multi-D, curved metric
-def _general_metric(X, Y, Z):
-    m = np.zeros((10,) + X.shape)
-    m[0] = 0.85 + 0.1 * np.sin(2 * math.pi * X) * np.cos(2 * math.pi * Y)
-    m[1] = 0.05 * np.sin(2 * math.pi * Y)
-    m[2] = -0.03 * np.cos(2 * math.pi * Z)
-    m[3] = 0.02 * np.sin(2 * math.pi * X)
-    psi4 = 1.2 + 0.1 * np.cos(2 * math.pi * Z) * np.sin(2 * math.pi * X)
-    m[4] = psi4
-    m[7] = psi4 * 1.05
-    m[9] = psi4 * 0.95
-    m[5] = 0.02 * np.cos(2 * math.pi * Z)
-    m[6] = -0.015 * np.sin(2 * math.pi * Y)
-    m[8] = 0.01 * np.cos(2 * math.pi * X)
-    return m
-
-
 @pytest.mark.parametrize("dims,cleaning", [((37, 11, 7), False), ((37, 11, 7), True),
                                            ((70, 9, 1), True), ((33, 5, 66), False)])
 def test_curved_periodic_ragged(dims, cleaning):
     """General static metric (lapse, shift, non-diagonal gamma), periodic, several tiles with
     ragged tails in every direction, z chunks; with and without cleaning."""
     P = W.smooth_periodic(dims, seed=5, amp=0.2, magnetised=True)
-    P = W.with_periodic_metric(P, _general_metric)
+    P = W.with_periodic_metric(P, general_metric)
     if cleaning:
         P.cleaning, P.ch, P.kappa = True, 0.6, 0.7
         P.prim[8] = 0.01 * np.sin(np.arange(P.ncell).reshape(P.prim[8].shape) * 0.37)

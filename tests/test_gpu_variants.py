@@ -65,10 +65,10 @@ def test_ppm_blob_with_cleaning():
 
 
 def test_ppm_general_metric_periodic_3d():
-    from test_gpu_parity import _general_metric
+    from parity import general_metric
 
     P = W.smooth_periodic((19, 11, 7), seed=5, amp=0.2, magnetised=True)
-    P = _ppm(W.with_periodic_metric(P, _general_metric))
+    P = _ppm(W.with_periodic_metric(P, general_metric))
     P.cleaning, P.ch, P.kappa = True, 0.6, 0.7
     dt = _dt(P, 0.4)
     gp, _, gs = gpu_run(P, nsteps=2, dt=dt)
