@@ -283,6 +283,21 @@ int hz_step_noalloc(const hz_grid* grid, const hz_options* opts, const double* d
                     const double* d_prim_in, double* d_prim_out, double dt, int nsteps,
                     void* stream);
 
+/* ---- Self-test of the double-word arithmetic of HZ_FP64_DW ------------------------------
+ * Not a step of the method: it exposes the pair-of-FP32 operations the HZ_FP64_DW kernels use,
+ * so that their error bounds can be checked against exact arithmetic on the host.  For each
+ * i < n it splits d_a[i] and d_b[i] into pairs x, y (integer split, as the kernels load
+ * doubles) and writes, as the two floats (hi, lo) of each result widened to double,
+ *   d_out[(2 q) n + i] = hi, d_out[(2 q + 1) n + i] = lo   for q = 0 .. HZ_DW_NRESULTS - 1:
+ *   q = 0 x, 1 y, 2 x + y, 3 x - y, 4 x * y, 5 x / y, 6 sqrt(|x|), 7 1 / sqrt(|x|),
+ *   8 the half MC slope of (x, y) (the reconstruction's limited slope).
+ * d_a, d_b (n doubles) and d_out (2 HZ_DW_NRESULTS n doubles) are caller-owned device
+ * memory; the work is enqueued on stream.  Returns HZ_ERR_ARG for null pointers or n < 0,
+ * HZ_ERR_CUDA if the launch fails. */
+#define HZ_DW_NRESULTS 9
+int hz_dw_selftest(const double* d_a, const double* d_b, double* d_out, long long n,
+                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

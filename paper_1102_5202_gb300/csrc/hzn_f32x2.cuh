@@ -62,7 +62,8 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // pipe's rate on this GPU; these use the integer and FP32 pipes only)
 
 // double -> pair: hi = x with its mantissa truncated to 24 bits (exact bit copy), lo = the
-// remaining 29 mantissa bits as a float, then renormalised.  |x| below 2^-126 gives 0.
+// remaining 29 mantissa bits as a float, then renormalised.  |x| below 2^-126 gives 0; |x| must
+// be below 2^128 (the FP32 range).
 __device__ __forceinline__ f32x2 split(double x) {
   const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
   const unsigned sign = hw & 0x80000000u;
@@ -71,13 +72,15 @@ __device__ __forceinline__ f32x2 split(double x) {
   const unsigned mh = ((hw & 0xfffffu) << 3) | (lw >> 29);
   const float h = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | mh);
   // remainder rem < 2^29, worth rem 2^(e-52): rem = a 2^6 + b with a < 2^23, b < 2^6, each
-  // made exact in FP32 by the 2^23 offset trick, then scaled by 2^(e+12) 2^-64
+  // made exact in FP32 by the 2^23 offset trick, then scaled by 2^(e-52) (as 2^(e+12) 2^-64
+  // when 2^(e-52) is below the FP32 normal range)
   const unsigned rem = lw & 0x1fffffffu;
   const float fa = __fsub_rn(__uint_as_float(0x4b000000u | (rem >> 6)), 8388608.0f);
   const float fb = __fsub_rn(__uint_as_float(0x4b000000u | (rem & 63u)), 8388608.0f);
   const float r = __fmaf_rn(fa, 64.0f, fb);
-  const float sc = __uint_as_float((unsigned)(e + 12 + 127) << 23);
-  float l = __fmul_rn(__fmul_rn(r, sc), 5.421010862427522e-20f);  // 2^-64
+  const bool low = e < -74;
+  const float sc = __uint_as_float((unsigned)(e - 52 + (low ? 64 : 0) + 127) << 23);
+  float l = __fmul_rn(__fmul_rn(r, sc), low ? 5.421010862427522e-20f : 1.0f);  // 2^-64
   l = __uint_as_float(__float_as_uint(l) | sign);
   float zh, zl;
   zh = __fadd_rn(h, l);

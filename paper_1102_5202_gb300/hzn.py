@@ -31,8 +31,9 @@ HZ_C2P_2D, HZ_C2P_1D = 0, 1
 EXPORTED = (
     "hz_workspace_bytes", "hz_create", "hz_destroy", "hz_set_metric", "hz_set_primitives",
     "hz_get_primitives", "hz_get_conserved", "hz_step", "hz_step_cfl", "hz_max_speed",
-    "hz_get_stats", "hz_strerror", "hz_version", "hz_step_noalloc",
+    "hz_get_stats", "hz_strerror", "hz_version", "hz_step_noalloc", "hz_dw_selftest",
 )
+HZ_DW_NRESULTS = 9
 
 
 class hz_grid(ctypes.Structure):
@@ -106,6 +107,7 @@ def lib():
             L.hz_get_stats.argtypes = [vp, P(hz_stats)]
             L.hz_step_noalloc.argtypes = [P(hz_grid), P(hz_options), vp, vp, vp, ctypes.c_double,
                                           ctypes.c_int, vp]
+            L.hz_dw_selftest.argtypes = [vp, vp, vp, ctypes.c_longlong, vp]
             L.hz_strerror.argtypes = [ctypes.c_int]
             L.hz_strerror.restype = ctypes.c_char_p
             L.hz_version.restype = ctypes.c_int
@@ -123,6 +125,18 @@ def hz_strerror(code: int) -> str:
 
 def hz_version() -> int:
     return int(lib().hz_version())
+
+
+def hz_dw_selftest(a, b):
+    """Double-word results of the HZ_FP64_DW arithmetic for the doubles a, b (1-D float64 CUDA
+    tensors of one length n): a (HZ_DW_NRESULTS, 2, n) float64 tensor of (hi, lo) per result."""
+    import torch
+
+    n = int(a.numel())
+    out = torch.empty((HZ_DW_NRESULTS, 2, n), dtype=torch.float64, device=a.device)
+    st = torch.cuda.current_stream(a.device).cuda_stream
+    _check(lib().hz_dw_selftest(a.data_ptr(), b.data_ptr(), out.data_ptr(), n, st), "hz_dw_selftest")
+    return out
 
 
 def hz_workspace_bytes(grid: hz_grid, opts: hz_options) -> int:
