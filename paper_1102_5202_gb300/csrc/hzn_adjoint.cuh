@@ -323,7 +323,7 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
   Geom<double> G;
   if constexpr (DIAG) {
     // face geometry of the diagonal metric from its table
-    G = geo_load<double>(kp.geo_f + D * GEO_N * kp.ms, o1, kp.ms);
+    G = geo_load<double>(kp.geo_f + D * GEO_F * kp.ms, o1, kp.ms);
   } else {
     double m[10];
     const long long o0 = o1 - (D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane));

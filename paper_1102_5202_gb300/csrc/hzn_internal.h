@@ -38,8 +38,9 @@ struct KParams {
   // Geometry tables of a metric with zero shift and diagonal gamma (filled by hz_set_metric,
   // used by the DIAG kernels), in the metric's padded layout (field stride ms):
   //   geo_c  centre geometry, GEO_N fields (both precisions; FP64 values);
-  //   geo_f  face geometry of axis d at geo_f + d GEO_N ms, the face i - 1/2 of cell (i, j, k)
-  //          at the cell's metric offset (FP64 path only);
+  //   geo_f  face geometry of axis d at geo_f + d GEO_F ms, the face i - 1/2 of cell (i, j, k)
+  //          at the cell's metric offset: the GEO_N fields of the centre table, then
+  //          alpha sqrt(gamma^dd) (the cleaning speed per unit c_h) (FP64 path only);
   //   geo_s  differences g(+1) - g(-1) of g_tt, g_xx, g_yy, g_zz along axis d at
   //          geo_s + d GEO_S ms (FP64 path only).
   const double* geo_c;
@@ -48,6 +49,7 @@ struct KParams {
 };
 
 constexpr int GEO_N = 10;  // alpha, 1/alpha, gamma_xx, _yy, _zz, gamma^xx, ^yy, ^zz, sqrt(gamma), sqrt(-g)
+constexpr int GEO_F = GEO_N + 1;  // face tables: GEO_N fields and alpha sqrt(gamma^dd)
 constexpr int GEO_S = 4;   // g_tt, g_xx, g_yy, g_zz
 
 // One substep: Uout = a0 U0 + ak (Uk + dt L(Pin)); Pout = primitives of Uout.

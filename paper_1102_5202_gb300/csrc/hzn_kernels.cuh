@@ -113,10 +113,11 @@ __device__ __forceinline__ void load_metric(const KParams& kp, const S* __restri
 
 // HLLE flux (§2.2) of one face from its reconstructed left / right primitive states and face
 // geometry, written to out[f * ostride].  ROLL: one copy of the state code serves both states
-// (a loop the compiler keeps rolled), which halves the code of the double-word path.
+// (a loop the compiler keeps rolled), which halves the code of the double-word path.  cfac:
+// alpha sqrt(gamma^DD) at the face (used with cleaning on a DIAG metric).
 template <int D, bool CLEAN, bool DIAG, bool ROLL, typename R>
 __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const R PR[9],
-                                          const Consts<R>& c, R* out, int ostride) {
+                                          const Consts<R>& c, R cfac, R* out, int ostride) {
   constexpr int NV = CLEAN ? 9 : 8;
   // wave speeds.  FP64: both states' quadratics, multiplied through by w (w + b^2), share one
   // division 0.5 / (A'_L A'_R).  FP32 (mixed) and double-word: the plain quadratic per state,
@@ -196,15 +197,23 @@ __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const
 #pragma unroll
   for (int f = 0; f < NV; ++f) out[f * ostride] = wl * FL[f] + (wr * FR[f] + wu * (UR[f] - UL[f]));
   if (CLEAN) {
-    R cm, cp;
-    clean_speeds<D, DIAG>(G, c.ch, cm, cp);
-    const R csl = fmin(R(0), cm), csr = fmax(R(0), cp);
-    const R cden = csr - csl;
     const int fb = U_BX + D;
-    if (cden != R(0)) {
-      const R ic = G.sqrtmg / cden;
-      out[fb * ostride] = (csr * FL[fb] - csl * FR[fb] + csl * csr * (UR[fb] - UL[fb])) * ic;
-      out[U_PSI * ostride] = (csr * FL[U_PSI] - csl * FR[U_PSI] + csl * csr * (UR[U_PSI] - UL[U_PSI])) * ic;
+    if constexpr (DIAG) {
+      // zero shift: the pair's bounds are -+a, a = c_h alpha sqrt(gamma^DD) > 0, so the weights
+      // reduce to sqrt(-g) / 2 for each state and a sqrt(-g) / 2 for the jump
+      const R hs = R(0.5) * G.sqrtmg, ha = hs * (c.ch * cfac);
+      out[fb * ostride] = hs * (FL[fb] + FR[fb]) - ha * (UR[fb] - UL[fb]);
+      out[U_PSI * ostride] = hs * (FL[U_PSI] + FR[U_PSI]) - ha * (UR[U_PSI] - UL[U_PSI]);
+    } else {
+      R cm, cp;
+      clean_speeds<D, DIAG>(G, c.ch, cm, cp);
+      const R csl = fmin(R(0), cm), csr = fmax(R(0), cp);
+      const R cden = csr - csl;
+      if (cden != R(0)) {
+        const R ic = G.sqrtmg / cden;
+        out[fb * ostride] = (csr * FL[fb] - csl * FR[fb] + csl * csr * (UR[fb] - UL[fb])) * ic;
+        out[U_PSI * ostride] = (csr * FL[U_PSI] - csl * FR[U_PSI] + csl * csr * (UR[U_PSI] - UL[U_PSI])) * ic;
+      }
     }
   }
 }
@@ -247,7 +256,7 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
   // face metric: mean of the two adjacent centre values (tabulated for a DIAG metric in FP64)
   Geom<R> G;
   if constexpr (DIAG && !SameType<R, float>::value) {
-    G = geo_load<R>(kp.geo_f + D * GEO_N * kp.ms, met_off(kp, i, j, k), kp.ms);
+    G = geo_load<R>(kp.geo_f + D * GEO_F * kp.ms, met_off(kp, i, j, k), kp.ms);
   } else {
     R m[10];
     const long long o1 = met_off(kp, i, j, k);
@@ -260,7 +269,14 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
     G = make_geom<DIAG>(m);
   }
   const Consts<R> c = consts_of<R>(kp);
-  hlle_face<D, CLEAN, DIAG, false>(G, PL, PR, c, out, ostride);
+  R cfac = R(0);
+  if constexpr (CLEAN && DIAG) {
+    if constexpr (!SameType<R, float>::value)
+      cfac = ldc<R>(kp.geo_f + (D * GEO_F + GEO_N) * kp.ms + met_off(kp, i, j, k));
+    else
+      cfac = G.alp * sqrt(sel<D>(G.ixx, G.iyy, G.izz));
+  }
+  hlle_face<D, CLEAN, DIAG, false>(G, PL, PR, c, cfac, out, ostride);
 }
 
 // One face of the double-word path with its direction D given at run time (one copy of the
@@ -310,7 +326,7 @@ __device__ __forceinline__ void face_flux_dw(const KParams& kp, const double* __
   Geom<R> G;
   const long long mo = met_off(kp, i, j, k);
   if constexpr (DIAG) {
-    G = geo_load<R>(kp.geo_f + D * GEO_N * kp.ms, mo, kp.ms);
+    G = geo_load<R>(kp.geo_f + D * GEO_F * kp.ms, mo, kp.ms);
     const R g0 = G.gxx, g1 = G.gyy, g2 = G.gzz, h0 = G.ixx, h1 = G.iyy, h2 = G.izz;
     G.gxx = pick(c0, g0, g1, g2);
     G.gyy = pick(c1, g0, g1, g2);
@@ -350,8 +366,10 @@ __device__ __forceinline__ void face_flux_dw(const KParams& kp, const double* __
     G = make_geom<false>(r);
   }
   const Consts<R> c = consts_of<R>(kp);
+  R cfac = R(0);
+  if constexpr (CLEAN && DIAG) cfac = ldc<R>(kp.geo_f + (D * GEO_F + GEO_N) * kp.ms + mo);
   R F[9];
-  hlle_face<0, CLEAN, DIAG, true>(G, PL, PR, c, F, 1);
+  hlle_face<0, CLEAN, DIAG, true>(G, PL, PR, c, cfac, F, 1);
   // rotate back: rotated component a is original component (D + a) mod 3
   R T[3] = {F[U_TX], F[U_TY], F[U_TZ]}, B[3] = {F[U_BX], F[U_BY], F[U_BZ]};
   auto back = [&](int orig, const R v[3]) {
@@ -892,7 +910,9 @@ __global__ void k_geo_tables(const KParams kp, const S* __restrict__ M, double* 
         load_metric<true>(kp, M, mo, m1);
 #pragma unroll
         for (int f = 0; f < 10; ++f) m[f] = 0.5 * (m0[f] + m1[f]);
-        geo_store(gf + d * GEO_N * kp.ms, mo, kp.ms, make_geom<true>(m));
+        const Geom<double> Gf = make_geom<true>(m);
+        geo_store(gf + d * GEO_F * kp.ms, mo, kp.ms, Gf);
+        gf[(d * GEO_F + GEO_N) * kp.ms + mo] = Gf.alp * sqrt(d == 0 ? Gf.ixx : (d == 1 ? Gf.iyy : Gf.izz));
       }
       if (cell) {
         const G4<double> gp = g4_at<true, double>(kp, M, mo + st), gm = g4_at<true, double>(kp, M, mo - st);
