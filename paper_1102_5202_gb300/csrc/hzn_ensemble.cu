@@ -21,7 +21,7 @@
 #include <vector>
 
 #include "hzn.h"
-#include "hzn_physics.cuh"
+#include "hzn_kernels.cuh"
 
 using namespace hzn;
 
@@ -86,31 +86,11 @@ __device__ __forceinline__ void tube_face(const double* P, long long fs, int n, 
     PR[q] = cc - mc_half_slope(d1, d2);
   }
   PL[8] = PR[8] = 0.0;
-  double FL[9], UL[9], FR[9], UR[9], lmL, lpL, lmR, lpR;
-  {
-    const State<double> S = make_state<true>(G, PL, c);
-    flux_of<0, false, true>(G, S, c, FL);
-    cons_of<false>(G, S, UL);
-    speeds_of<0, true>(G, S, cms2_of(S, c), lmL, lpL);
-  }
-  {
-    const State<double> S = make_state<true>(G, PR, c);
-    flux_of<0, false, true>(G, S, c, FR);
-    cons_of<false>(G, S, UR);
-    speeds_of<0, true>(G, S, cms2_of(S, c), lmR, lpR);
-  }
-  const double sl = fmin(0.0, fmin(lmL, lmR));
-  const double sr = fmax(0.0, fmax(lpL, lpR));
-  const double den = sr - sl;
-  double wl = 0.5, wr = 0.5, wu = 0.0;
-  if (den != 0.0) {
-    const double iden = 1.0 / den;
-    wl = sr * iden;
-    wr = -sl * iden;
-    wu = sl * sr * iden;
-  }
+  // the grid kernel's HLLE of one face (FP64: both roots as fractions, one division)
+  double F9[9];
+  hlle_face<0, false, true, false>(G, PL, PR, c, 0.0, F9, 1);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) F[q] = wl * FL[q] + (wr * FR[q] + wu * (UR[q] - UL[q]));
+  for (int q = 0; q < 8; ++q) F[q] = F9[q];
 }
 
 __device__ __forceinline__ double cell_speed(const double* P, long long fs, int i, const Geom<double>& G,

@@ -119,10 +119,10 @@ template <int D, bool CLEAN, bool DIAG, bool ROLL, typename R>
 __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const R PR[9],
                                           const Consts<R>& c, R cfac, R* out, int ostride) {
   constexpr int NV = CLEAN ? 9 : 8;
-  // wave speeds.  FP64: both states' quadratics, multiplied through by w (w + b^2), share one
-  // division 0.5 / (A'_L A'_R).  FP32 (mixed) and double-word: the plain quadratic per state,
-  // since A' scales like w^2 and the product underflows the FP32 exponent range in near-vacuum
-  // cells.
+  // wave speeds.  FP64: both states' quadratics, multiplied through by w (w + b^2); their roots
+  // enter the HLLE weights as fractions, with one division per face.  FP32 (mixed) and
+  // double-word: the plain quadratic per state, since A' scales like w^2 and the cross products
+  // underflow the FP32 exponent range in near-vacuum cells.
   constexpr bool SHARED = SameType<R, double>::value && !ROLL;
   R FL[9], UL[9], AL, BL, sqL, lmL, lpL;
   R FR[9], UR[9], AR, BR, sqR, lmR, lpR;
@@ -171,28 +171,51 @@ __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const
       else speeds_of<D, DIAG>(G, St, cms2_of(St, c), lmR, lpR);
     }
   }
-  if constexpr (SHARED) {
-    const R ia = R(0.5) / (AL * AR);
-    const R i2aL = AR * ia, i2aR = AL * ia;
-    lpL = (-BL + sqL) * i2aL;
-    lmL = (-BL - sqL) * i2aL;
-    lpR = (-BR + sqR) * i2aR;
-    lmR = (-BR - sqR) * i2aR;
-  }
   // HLLE: F = (sR FL - sL FR + sL sR (UR - UL)) / (sR - sL).  FL, FR, UL, UR are the vectors
   // divided by sqrt(-g) (the face's, common to both states), folded back into the weights.
-  const R sl = fmin(R(0), fmin(lmL, lmR));
-  const R sr = fmax(R(0), fmax(lpL, lpR));
-  const R den = sr - sl;
   R wl, wr, wu;
-  if (den != R(0)) {
-    const R iden = G.sqrtmg / den;
-    wl = sr * iden;
-    wr = -sl * iden;
-    wu = sl * sr * iden;
+  if constexpr (SHARED) {
+    // The roots are (-b -+ sq) / A' with A' > 0.  The bounds sL = min(0, lambda-), sR =
+    // max(0, lambda+) are chosen by cross-multiplied comparisons and kept as fractions n / d
+    // (n = 0, d = 1 for a bound clamped at 0); then wL = nR dL / Q, wR = -nL dR / Q and
+    // wU = nL nR / Q with Q = nR dL - nL dR, so one division serves the face.
+    const R nmL = -BL - sqL, nmR = -BR - sqR, npL = -BL + sqL, npR = -BR + sqR;
+    const R dL = AL, dR = AR;
+    const bool lowL = nmL * dR < nmR * dL;
+    R nl = lowL ? nmL : nmR, dl = lowL ? dL : dR;
+    if (!(nl < R(0))) {
+      nl = R(0);
+      dl = R(1);
+    }
+    const bool highL = npL * dR > npR * dL;
+    R nr = highL ? npL : npR, dr = highL ? dL : dR;
+    if (!(nr > R(0))) {
+      nr = R(0);
+      dr = R(1);
+    }
+    const R q = nr * dl - nl * dr;
+    if (q != R(0)) {
+      const R iq = G.sqrtmg / q;
+      wl = nr * dl * iq;
+      wr = -nl * dr * iq;
+      wu = nl * nr * iq;
+    } else {
+      wl = wr = R(0.5) * G.sqrtmg;
+      wu = R(0);
+    }
   } else {
-    wl = wr = R(0.5) * G.sqrtmg;
-    wu = R(0);
+    const R sl = fmin(R(0), fmin(lmL, lmR));
+    const R sr = fmax(R(0), fmax(lpL, lpR));
+    const R den = sr - sl;
+    if (den != R(0)) {
+      const R iden = G.sqrtmg / den;
+      wl = sr * iden;
+      wr = -sl * iden;
+      wu = sl * sr * iden;
+    } else {
+      wl = wr = R(0.5) * G.sqrtmg;
+      wu = R(0);
+    }
   }
 #pragma unroll
   for (int f = 0; f < NV; ++f) out[f * ostride] = wl * FL[f] + (wr * FR[f] + wu * (UR[f] - UL[f]));
@@ -590,6 +613,7 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   const int kz1 = min(kz0 + kp.zlen, kp.nz);
   const bool own = i < kp.nx && j < kp.ny;
   const double dt = sc->dt;
+  const bool first_stage = sa.a0 == 0.0 && sa.ak == 1.0;  // U = Uk + dt L
   const Consts<R> c = consts_of<R>(kp);
   const Consts<double> cd = consts_of<double>(kp);
   const R ridx = cvt<R>(kp.idx), ridy = cvt<R>(kp.idy), ridz = cvt<R>(kp.idz);
@@ -746,8 +770,9 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
 #pragma unroll
       for (int f = 0; f < NV; ++f) {
         const double uk = sa.Uk[f * kp.fs + off];
-        double u = sa.ak * (uk + dt * to_dbl(L[f]));
-        if (sa.a0 != 0.0) u += sa.a0 * sa.U0[f * kp.fs + off];
+        double u;
+        if (first_stage) u = uk + dt * to_dbl(L[f]);
+        else u = sa.ak * (uk + dt * to_dbl(L[f])) + sa.a0 * sa.U0[f * kp.fs + off];
         U[f] = u;
       }
       if (!CLEAN) U[8] = 0.0;

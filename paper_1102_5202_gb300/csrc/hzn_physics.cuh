@@ -305,8 +305,8 @@ __device__ __forceinline__ void speeds_of(const Geom<R>& G, const State<R>& S, R
 }
 
 // The same quadratic multiplied through by w (w + b^2), so that c^2 = N / Dd enters without a
-// division: A' = (Dd - N) (u^t)^2 + N / alpha^2, B', C' likewise; its roots are the speeds.
-// Returns A', B' and sqrt(max(B'^2 - 4 A'C', 0)); lambda+- = (-B' +- sq) / (2 A').
+// division: A' = (Dd - N) (u^t)^2 + N / alpha^2, B', C' likewise, with B' halved: returns A',
+// b = B' / 2 and sq = sqrt(max(b^2 - A'C', 0)); the roots, the speeds, are (-b +- sq) / A'.
 template <int D, bool DIAG, typename R>
 __device__ __forceinline__ void speed_quadratic(const Geom<R>& G, const State<R>& S, const Consts<R>& c,
                                                 R& A, R& B, R& sq) {
@@ -320,16 +320,16 @@ __device__ __forceinline__ void speed_quadratic(const Geom<R>& G, const State<R>
   A = oc * S.ut * S.ut + N * ia2;
   R C;
   if constexpr (DIAG) {
-    B = R(-2) * (oc * S.ut * ud);
+    B = -(oc * S.ut * ud);
     C = oc * ud * ud - N * sel<D>(G.ixx, G.iyy, G.izz);
   } else {
     const R bd = sel<D>(G.bx, G.by, G.bz);
     const R gtd = bd * ia2;
     const R gdd = sel<D>(G.ixx, G.iyy, G.izz) - bd * bd * ia2;
-    B = R(-2) * (oc * S.ut * ud - N * gtd);
+    B = -(oc * S.ut * ud - N * gtd);
     C = oc * ud * ud - N * gdd;
   }
-  R disc = B * B - R(4) * A * C;
+  R disc = B * B - A * C;
   disc = disc > R(0) ? disc : R(0);
   sq = sqrt(disc);
 }
@@ -352,12 +352,15 @@ __device__ __forceinline__ void clean_speeds(const Geom<R>& G, R ch, R& lm, R& l
 // §3.2): sign(dp) min(|dm|, |dp|, |dm + dp| / 4) when dm and dp have the same strict sign,
 // else 0.  The face values are P_i -+ this.  For FP64 the sign test and the three-way minimum
 // are taken on the IEEE bit patterns (the order of non-negative doubles is the order of their
-// bits), so that only the sum and the exact quarter run on the FP64 pipe; the result is the
-// same number the floating-point comparisons give.
+// bits) and the quarter by exponent arithmetic, so that only the sum runs on the FP64 pipe; the
+// result is the number the floating-point operations give (for |dm + dp| >= 2^-1020).
 __device__ __forceinline__ double mc_half_slope(double dm, double dp) {
   const long long bm = __double_as_longlong(dm), bp = __double_as_longlong(dp);
   const long long am = bm & 0x7fffffffffffffffLL, ap = bp & 0x7fffffffffffffffLL;
-  const long long aq = __double_as_longlong(0.25 * (dm + dp)) & 0x7fffffffffffffffLL;
+  // |dm + dp| / 4 by lowering the exponent field by 2: exact for |dm + dp| >= 2^-1020, and
+  // taken as 0 below that (no FP64 multiply)
+  const long long as = __double_as_longlong(dm + dp) & 0x7fffffffffffffffLL;
+  const long long aq = as >= (3LL << 52) ? as - (2LL << 52) : 0LL;
   long long m = am < ap ? am : ap;
   m = m < aq ? m : aq;
   const bool same = ((bm ^ bp) >= 0) && am != 0 && ap != 0;
