@@ -40,15 +40,20 @@ FP64_PEAK_TFLOPS = 1.194
 # FP64 operations per cell per substep executed by the fused substep kernel (3-D, cleaning
 # on, diagonal metric with its geometry tables), from ncu instruction counters on the 128^3
 # blob (profiles/k_substep_blob3d.md): DFMA counted as 2 flops, DADD/DMUL as 1.
-FP64_FLOPS_PER_CELL_SUBSTEP = 2133.8
+FP64_FLOPS_PER_CELL_SUBSTEP = 1853.3
+# FP64 instructions (DFMA + DMUL + DADD) per cell per substep from the same capture, and the
+# FP64 instruction rate of the pipe measured by the probe (1.91 DFMA per clock per SM at
+# 2070 MHz): DMUL and DADD occupy the pipe like a DFMA, so this fraction is the pipe's use.
+FP64_INST_PER_CELL_SUBSTEP = 1419.9
+FP64_INST_PEAK_PER_S = 6.0e11
 # DRAM bytes per cell per substep of the same kernel from the same capture (read + write,
-# 1501 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
-DRAM_BYTES_PER_CELL_SUBSTEP = 688.4
+# 1502 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
+DRAM_BYTES_PER_CELL_SUBSTEP = 716.1
 # The same two figures for the mixed-precision substep kernel at 256^3
 # (profiles/k_substep_mixed_blob3d.md): FP64 flops (recovery, update) per cell per substep,
 # and DRAM bytes per cell per substep.
-MIXED_FP64_FLOPS_PER_CELL_SUBSTEP = 157.7
-MIXED_DRAM_BYTES_PER_CELL_SUBSTEP = 326.7
+MIXED_FP64_FLOPS_PER_CELL_SUBSTEP = 148.7
+MIXED_DRAM_BYTES_PER_CELL_SUBSTEP = 323.6
 # Algorithmic HBM bytes per zone update (three substeps, FP64, nine fields): read P, U_k, U0,
 # metric and write U_{k+1}, P_{k+1} once per substep; stage 1 reads U0 once.
 HBM_BYTES_PER_ZU = (46 + 55 + 55) * 8
@@ -216,6 +221,9 @@ def run_gpu(args, rank, world, local):
                 "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": DRAM_BYTES_PER_CELL_SUBSTEP * cells if DRAM_BYTES_PER_CELL_SUBSTEP else None,
                 "kernel": "k_substep<32,4,3-D,cleaning,diag,FP64,MC>", "peak_source": "measured FP64 DFMA loop"}
+        inst = FP64_INST_PER_CELL_SUBSTEP * cells / substep_s
+        roof["fp64_instructions"] = {"per_cell_substep": FP64_INST_PER_CELL_SUBSTEP, "achieved_per_s": inst,
+                                     "peak_per_s": FP64_INST_PEAK_PER_S, "frac": inst / FP64_INST_PEAK_PER_S}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "kernel": "k_substep<32,4,3-D,cleaning>"}
