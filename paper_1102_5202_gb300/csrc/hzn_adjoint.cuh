@@ -243,7 +243,8 @@ __device__ __forceinline__ void speeds_rev(const Geom<double>& G, const State<do
   const double gp = c.gamma * S.p;
   const double wt = S.w + S.b2;
   const double N = gp * wt + S.b2 * (S.w - gp), Dd = S.w * wt;
-  const double c2 = N / Dd;
+  const double iDd = 1.0 / Dd;
+  const double c2 = N * iDd;
   const double ia2 = G.ialp * G.ialp;
   const double ud = sel<D>(S.ux, S.uy, S.uz);
   const double oc = 1.0 - c2;
@@ -257,7 +258,7 @@ __device__ __forceinline__ void speeds_rev(const Geom<double>& G, const State<do
   const double sq = disc > 0.0 ? sqrt(disc) : 0.0;
   const double i2a = 0.5 / A;
   const double lp = (-B + sq) * i2a, lm = (-B - sq) * i2a;
-  double Ab = -(lpb * lp + lmb * lm) / A;
+  double Ab = -(lpb * lp + lmb * lm) * (i2a + i2a);  // / A
   double Bb = -i2a * (lpb + lmb);
   double Cb = 0.0;
   if (disc > 0.0) {
@@ -270,7 +271,7 @@ __device__ __forceinline__ void speeds_rev(const Geom<double>& G, const State<do
   const double utb = 2.0 * Ab * oc * S.ut - 2.0 * Bb * oc * ud;
   const double udb = -2.0 * Bb * oc * S.ut + 2.0 * Cb * oc * ud;
   double c2b = Ab * ia2 + 2.0 * Bb * gtd - Cb * gdd - ocb;
-  const double Nb = c2b / Dd, Ddb = -c2b * c2 / Dd;
+  const double Nb = c2b * iDd, Ddb = -c2b * c2 * iDd;
   const double gpb = Nb * (wt - S.b2);
   const double wtb = Nb * gp + Ddb * S.w;
   s.b2 += Nb * (S.w - gp) + wtb;
@@ -355,6 +356,7 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
   const bool sr_on = 0.0 < pi;
   const double sr = sr_on ? pi : 0.0;
   const double den = sr - sl;
+  const double iden = den != 0.0 ? 1.0 / den : 0.0;
   double FLb[9], FRb[9], ULb[9], URb[9];
   double slb = 0.0, srb = 0.0;
   const int fb = U_BX + D;
@@ -365,7 +367,6 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
     if (CLEAN && (q == fb || q == U_PSI)) continue;
     const double g = Fb[q];
     if (den != 0.0) {
-      const double iden = 1.0 / den;
       const double dU = UR[q] - UL[q];
       const double F = (sr * FL[q] - sl * FR[q] + sl * sr * dU) * iden;
       FLb[q] = sr * iden * g;
