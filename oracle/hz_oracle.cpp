@@ -10,7 +10,7 @@
 //   ghost fill -> MC reconstruction of primitives (§2.2, §3.2) -> face metric -> flux and
 //   conserved vector of the left and right states -> fast-magnetosonic speeds -> HLLE face
 //   flux (§2.2, §3.2) -> flux divergence + metric source (§2.1 Eq. 2, §2.2) -> Runge-Kutta
-//   stage (§3.2) -> conservative-to-primitive recovery (§2.2 "Newton-Raphson", §3.2).
+//   stage (§3.2) -> conservative-to-primitive recovery (§2.2 Newton-Raphson iteration, §3.2).
 // Every step runs over the whole grid before the next one starts: no fusion, no tiling.
 //
 // Readings of points where the paper is silent (each one listed in the design doc):
