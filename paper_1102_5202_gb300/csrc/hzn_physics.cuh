@@ -374,6 +374,18 @@ __device__ __forceinline__ float mc_half_slope(float dm, float dp) {
   return dm * dp > 0.f ? s : 0.f;
 }
 
+// Half MC slope in double-word arithmetic (the same definition as the FP64 and FP32 versions:
+// sign(dp) min(|dm|, |dp|, |dm + dp| / 4) for a strict common sign, else 0; the sign of a
+// normalised pair is the sign of its leading float, and the quarter is exact).
+__device__ __forceinline__ f32x2 mc_half_slope(f32x2 dm, f32x2 dp) {
+  const bool same = (dm.hi > 0.0f && dp.hi > 0.0f) || (dm.hi < 0.0f && dp.hi < 0.0f);
+  if (!same) return f32x2(0.0f, 0.0f);
+  const f32x2 s = dm + dp;
+  const f32x2 aq(fabsf(s.hi) * 0.25f, (s.hi < 0.0f ? -s.lo : s.lo) * 0.25f);
+  const f32x2 m = fmin(fmin(fabs(dm), fabs(dp)), aq);
+  return dp.hi > 0.0f ? m : -m;
+}
+
 // PPM (§3.2; the piecewise parabolic method of Colella and Woodward as used by Marti and
 // Muller).  Interface value between cells a and b from their values and MC half slopes:
 //   e = (qa + qb)/2 - (sigma_b - sigma_a)/6 = (qa + qb)/2 - (hb - ha)/3,
