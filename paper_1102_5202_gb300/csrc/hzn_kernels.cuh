@@ -99,19 +99,6 @@ __device__ __forceinline__ void load_metric(const KParams& kp, const S* __restri
   }
 }
 
-// 1/x for the HLLE weights: the hardware reciprocal approximation refined by two Newton steps
-// (each doubles the correct bits; the result is within a few ulps of 1/x, which the weights,
-// shared by both neighbours of the face, tolerate without affecting conservation).  x is a
-// normal number.
-__device__ __forceinline__ double rcp_newton(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
 // HLLE flux (§2.2) of one face from its reconstructed left / right primitive states and face
 // geometry, written to out[f * ostride].  ROLL: one copy of the state code serves both states
 // (a loop the compiler keeps rolled), which halves the code of the double-word path.  cfac:
@@ -196,7 +183,7 @@ __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const
     }
     const R q = nr * dl - nl * dr;
     if (q != R(0)) {
-      const R iq = G.sqrtmg * rcp_newton(q);
+      const R iq = G.sqrtmg * rcp_fast(q);
       wl = nr * dl * iq;
       wr = -nl * dr * iq;
       wu = nl * nr * iq;
