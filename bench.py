@@ -40,15 +40,15 @@ FP64_PEAK_TFLOPS = 1.194
 # FP64 operations per cell per substep executed by the fused substep kernel (3-D, cleaning
 # on, diagonal metric with its geometry tables), from ncu instruction counters on the 128^3
 # blob (profiles/k_substep_blob3d.md): DFMA counted as 2 flops, DADD/DMUL as 1.
-FP64_FLOPS_PER_CELL_SUBSTEP = 1806.2
+FP64_FLOPS_PER_CELL_SUBSTEP = 1803.9
 # FP64 instructions (DFMA + DMUL + DADD) per cell per substep from the same capture, and the
 # FP64 instruction rate of the pipe measured by the probe (1.91 DFMA per clock per SM at
 # 2070 MHz): DMUL and DADD occupy the pipe like a DFMA, so this fraction is the pipe's use.
-FP64_INST_PER_CELL_SUBSTEP = 1393.0
+FP64_INST_PER_CELL_SUBSTEP = 1391.8
 FP64_INST_PEAK_PER_S = 6.0e11
 # DRAM bytes per cell per substep of the same kernel from the same capture (read + write,
-# 1505 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
-DRAM_BYTES_PER_CELL_SUBSTEP = 717.6
+# 1504 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
+DRAM_BYTES_PER_CELL_SUBSTEP = 717.1
 # The same two figures for the mixed-precision substep kernel at 256^3
 # (profiles/k_substep_mixed_blob3d.md): FP64 flops (recovery, update) per cell per substep,
 # and DRAM bytes per cell per substep.
