@@ -111,9 +111,10 @@ __device__ __forceinline__ void state_rev(const Geom<double>& G, const State<dou
     s.lz += G.bz * s.l_t;
   }
   // u^t = W / alpha, 1/u^t = alpha / W
-  s.W += s.ut * G.ialp - s.iut * S.iut / S.W;
+  const double iW = rcp_fast(S.W);
+  s.W += s.ut * G.ialp - s.iut * S.iut * iW;
   // W = sqrt(q), q = 1 + u_i u~^i
-  const double qb = 0.5 * s.W / S.W;
+  const double qb = 0.5 * s.W * iW;
   s.lx += P[P_UX] * qb;
   s.ly += P[P_UY] * qb;
   s.lz += P[P_UZ] * qb;
@@ -243,7 +244,7 @@ __device__ __forceinline__ void speeds_rev(const Geom<double>& G, const State<do
   const double gp = c.gamma * S.p;
   const double wt = S.w + S.b2;
   const double N = gp * wt + S.b2 * (S.w - gp), Dd = S.w * wt;
-  const double iDd = 1.0 / Dd;
+  const double iDd = rcp_fast(Dd);
   const double c2 = N * iDd;
   const double ia2 = G.ialp * G.ialp;
   const double ud = sel<D>(S.ux, S.uy, S.uz);
@@ -255,14 +256,15 @@ __device__ __forceinline__ void speeds_rev(const Geom<double>& G, const State<do
   const double B = -2.0 * (oc * S.ut * ud - c2 * gtd);
   const double C = oc * ud * ud - c2 * gdd;
   const double disc = B * B - 4.0 * A * C;
-  const double sq = disc > 0.0 ? sqrt(disc) : 0.0;
-  const double i2a = 0.5 / A;
+  const double rsq = disc > 0.0 ? rsqrt(disc) : 0.0;
+  const double sq = disc * rsq;
+  const double i2a = 0.5 * rcp_fast(A);
   const double lp = (-B + sq) * i2a, lm = (-B - sq) * i2a;
   double Ab = -(lpb * lp + lmb * lm) * (i2a + i2a);  // / A
   double Bb = -i2a * (lpb + lmb);
   double Cb = 0.0;
   if (disc > 0.0) {
-    const double discb = i2a * (lpb - lmb) * 0.5 / sq;
+    const double discb = i2a * (lpb - lmb) * 0.5 * rsq;
     Bb += 2.0 * B * discb;
     Ab -= 4.0 * C * discb;
     Cb -= 4.0 * A * discb;
@@ -356,7 +358,7 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
   const bool sr_on = 0.0 < pi;
   const double sr = sr_on ? pi : 0.0;
   const double den = sr - sl;
-  const double iden = den != 0.0 ? 1.0 / den : 0.0;
+  const double iden = den != 0.0 ? rcp_fast(den) : 0.0;
   double FLb[9], FRb[9], ULb[9], URb[9];
   double slb = 0.0, srb = 0.0;
   const int fb = U_BX + D;
@@ -385,7 +387,7 @@ __device__ void face_rev(const KParams& kp, const double* __restrict__ P, const 
     clean_speeds<D, DIAG>(G, c.ch, cm, cp);
     const double csl = fmin(0.0, cm), csr = fmax(0.0, cp);
     const double cden = csr - csl;
-    const double ic = 1.0 / cden;
+    const double ic = rcp_fast(cden);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const int q = t == 0 ? fb : U_PSI;
@@ -577,7 +579,7 @@ __device__ __forceinline__ void elim5(double At[5][5], double r[5], double inv[5
         r[rr] = t;
       }
     }
-    inv[COL] = 1.0 / At[COL][COL];
+    inv[COL] = rcp_fast(At[COL][COL]);
 #pragma unroll
     for (int rr = COL + 1; rr < 5; ++rr) {
       const double fct = At[rr][COL] * inv[COL];
@@ -632,7 +634,7 @@ __device__ __forceinline__ void ift(const Geom<double>& G, const State<double>& 
   jac_row<4, CLEAN, DIAG>(G, S, Pc, c, At, Cb);
   double x[5] = {lamP[0], lamP[1], lamP[2], lamP[3], lamP[4]};
   solve5(At, x);
-  const double isg = 1.0 / G.sqrtmg;
+  const double isg = rcp_fast(G.sqrtmg);
 #pragma unroll
   for (int m = 0; m < 5; ++m) mu[m] = x[m];
 #pragma unroll
@@ -642,7 +644,7 @@ __device__ __forceinline__ void ift(const Geom<double>& G, const State<double>& 
     for (int kq = 0; kq < 5; ++kq) t -= Cb[kq][q] * x[kq];
     mu[P_BX + q] = t * isg;
   }
-  mu[8] = CLEAN ? lamP[8] / G.sqrtg : 0.0;
+  mu[8] = CLEAN ? lamP[8] * rcp_fast(G.sqrtg) : 0.0;
 }
 
 // One thread per face of every active axis: flux adjoint from lam_L, face reverse, store the
