@@ -14,7 +14,10 @@
 //   mixed path  primitives and metric stored in float; reconstruction, face fluxes, HLLE and
 //               sources in float with the flux divergence accumulated in float; the RK update
 //               of the conserved state (stored in double), the recovery and the CFL maximum
-//               in double.
+//               in double;
+//   pair path   the FP64 path's storage, update, recovery and CFL maximum, with
+//               reconstruction, face states, fluxes, HLLE, divergence and sources in
+//               double-word arithmetic (hzn_f32x2.cuh) on the FP32 pipes.
 //
 // Grid storage: structure of arrays, x fastest, rows padded to 16 elements; the metric carries
 // its ghost layer; primitive boundaries are applied as clamped (outflow) or wrapped (periodic)
