@@ -6,7 +6,8 @@
 // scheme in the unknowns Z = rho h W^2 and v^2).
 //
 // Everything is written for the real type R (double for the FP64 path; float for the face,
-// flux and source work of the mixed-precision path) and for two metric classes: DIAG (zero
+// flux and source work of the mixed-precision path; the double-word f32x2 of hzn_f32x2.cuh for
+// the pair path) and for two metric classes: DIAG (zero
 // shift, diagonal gamma_ij -- Minkowski, isotropic and conformally flat static metrics) and
 // the general 3+1 metric.  DIAG drops terms that are identically zero, nothing else.
 //
