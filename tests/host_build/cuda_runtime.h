@@ -1,8 +1,8 @@
-// Stand-in for <cuda_runtime.h> in the host build of the double-word arithmetic (test harness
-// only; the product is built with nvcc).  The CUDA qualifiers expand to nothing and each device
+// Stand-in for <cuda_runtime.h> in the host builds of the device headers (test harnesses only;
+// the product is built with nvcc).  The CUDA qualifiers expand to nothing and each device
 // intrinsic the headers use is written with host IEEE arithmetic: float and double operations
-// rounded to nearest, std::fma for the fused multiply-add, bit copies through memcpy.  The one
-// approximations, rsqrtf and rsqrt, are 1/sqrt here (the device's are within 2 and 1 ulps).
+// rounded to nearest, std::fma for the fused multiply-add, bit copies through memcpy.  The
+// approximations rsqrtf and rsqrt are 1/sqrt here (the device's are within 2 and 1 ulps).
 #pragma once
 #include <cmath>
 #include <cstdint>
@@ -20,6 +20,7 @@ inline float __fmaf_rn(float a, float b, float c) { return std::fma(a, b, c); }
 inline float __frcp_rn(float a) { return 1.0f / a; }
 inline float rsqrtf(float a) { return 1.0f / std::sqrt(a); }
 inline double rsqrt(double a) { return 1.0 / std::sqrt(a); }
+inline float rsqrt(float a) { return 1.0f / std::sqrt(a); }
 
 inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
 inline float __uint_as_float(unsigned u) { float f; std::memcpy(&f, &u, 4); return f; }

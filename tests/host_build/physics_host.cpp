@@ -1,0 +1,112 @@
+// Host build of the pointwise device physics of hzn_physics.cuh in FP64 for a general 3+1
+// metric (the product's own templates, with the stand-in cuda_runtime.h of this folder), so
+// that the CPU tests can compare them with the oracle's pointwise functions.  Layouts are the
+// oracle's: met n x 10 (alpha, beta^i, gamma_xx, _xy, _xz, _yy, _yz, _zz), prim and cons n x 9,
+// row-major.
+#include "hzn_physics.cuh"
+
+using namespace hzn;
+
+namespace {
+
+Consts<double> consts(double gamma, double ch) {
+  Consts<double> c;
+  c.gamma = gamma;
+  c.gfac = gamma / (gamma - 1.0);
+  c.ch = ch;
+  c.ch2 = ch * ch;
+  return c;
+}
+
+template <int D, bool CLEAN>
+void flux_at(const Geom<double>& G, const State<double>& S, const Consts<double>& c, double* F) {
+  flux_of<D, CLEAN, false>(G, S, c, F);
+}
+
+template <int D>
+void speeds_at(const Geom<double>& G, const State<double>& S, const Consts<double>& c, double* lam,
+               double* lam_q) {
+  double lm, lp;
+  speeds_of<D, false>(G, S, cms2_of(S, c), lm, lp);
+  lam[0] = lm;
+  lam[1] = lp;
+  // the FP64 path's form: w(w + b^2) times the quadratic, halved linear coefficient
+  double A, b, sq;
+  speed_quadratic<D, false>(G, S, c, A, b, sq);
+  lam_q[0] = (-b - sq) / A;
+  lam_q[1] = (-b + sq) / A;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dev_prim2cons(long n, double gamma, int clean, const double* met, const double* prim,
+                   double* cons) {
+  const Consts<double> c = consts(gamma, 0.0);
+  for (long i = 0; i < n; ++i) {
+    const Geom<double> G = make_geom<false>(met + 10 * i);
+    double P[9];
+    for (int f = 0; f < 9; ++f) P[f] = prim[9 * i + f];
+    if (!clean) P[8] = 0.0;
+    const State<double> S = make_state<false>(G, P, c);
+    if (clean) cons_of<true>(G, S, cons + 9 * i);
+    else {
+      cons_of<false>(G, S, cons + 9 * i);
+      cons[9 * i + 8] = 0.0;
+    }
+  }
+}
+
+void dev_flux(long n, double gamma, double ch, int clean, int d, const double* met,
+              const double* prim, double* F) {
+  const Consts<double> c = consts(gamma, ch);
+  for (long i = 0; i < n; ++i) {
+    const Geom<double> G = make_geom<false>(met + 10 * i);
+    double P[9];
+    for (int f = 0; f < 9; ++f) P[f] = prim[9 * i + f];
+    if (!clean) P[8] = 0.0;
+    const State<double> S = make_state<false>(G, P, c);
+    double* o = F + 9 * i;
+    o[8] = 0.0;
+    if (clean) {
+      if (d == 0) flux_at<0, true>(G, S, c, o);
+      else if (d == 1) flux_at<1, true>(G, S, c, o);
+      else flux_at<2, true>(G, S, c, o);
+    } else {
+      if (d == 0) flux_at<0, false>(G, S, c, o);
+      else if (d == 1) flux_at<1, false>(G, S, c, o);
+      else flux_at<2, false>(G, S, c, o);
+    }
+  }
+}
+
+void dev_speeds(long n, double gamma, int d, const double* met, const double* prim, double* lam,
+                double* lam_q) {
+  const Consts<double> c = consts(gamma, 0.0);
+  for (long i = 0; i < n; ++i) {
+    const Geom<double> G = make_geom<false>(met + 10 * i);
+    const State<double> S = make_state<false>(G, prim + 9 * i, c);
+    if (d == 0) speeds_at<0>(G, S, c, lam + 2 * i, lam_q + 2 * i);
+    else if (d == 1) speeds_at<1>(G, S, c, lam + 2 * i, lam_q + 2 * i);
+    else speeds_at<2>(G, S, c, lam + 2 * i, lam_q + 2 * i);
+  }
+}
+
+// Recovery (the 2D Newton with its FP32 start and bracketed fallback) from the conserved
+// vector and a guess; status[i] = 1 when it failed.
+void dev_con2prim(long n, double gamma, int clean, const double* met, const double* cons,
+                  const double* guess, double tol, int maxit, double* prim, int* status) {
+  const Consts<double> c = consts(gamma, 0.0);
+  for (long i = 0; i < n; ++i) {
+    const Geom<double> G = make_geom<false>(met + 10 * i);
+    double P[9];
+    C2PResult r;
+    if (clean) r = con2prim<true, false>(G, cons + 9 * i, guess + 9 * i, c, maxit, 0.01 * std::sqrt(tol), P);
+    else r = con2prim<false, false>(G, cons + 9 * i, guess + 9 * i, c, maxit, 0.01 * std::sqrt(tol), P);
+    for (int f = 0; f < 9; ++f) prim[9 * i + f] = P[f];
+    status[i] = r.ok ? 0 : 1;
+  }
+}
+
+}  // extern "C"

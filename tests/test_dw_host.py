@@ -1,5 +1,5 @@
 """The double-word operations of the HZ_FP64_DW path built for the host (the product's headers
-with a stand-in for cuda_runtime.h, tests/dw_host/) against exact decimal arithmetic: the same
+with a stand-in for cuda_runtime.h, tests/host_build/) against exact decimal arithmetic: the same
 bounds as the GPU self-test, without a GPU."""
 import ctypes
 import os
@@ -19,7 +19,7 @@ CSRC = os.path.join(os.path.dirname(HERE), "paper_1102_5202_gb300", "csrc")
 def host_lib():
     out = os.path.join(tempfile.mkdtemp(prefix="dw_host_"), "dw_host.so")
     cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           "-I", os.path.join(HERE, "dw_host"), "-I", CSRC, os.path.join(HERE, "dw_host", "dw_host.cpp"),
+           "-I", os.path.join(HERE, "host_build"), "-I", CSRC, os.path.join(HERE, "host_build", "dw_host.cpp"),
            "-o", out]
     subprocess.run(cmd, check=True)
     L = ctypes.CDLL(out)
