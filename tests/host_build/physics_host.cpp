@@ -18,38 +18,34 @@ Consts<double> consts(double gamma, double ch) {
   return c;
 }
 
-template <int D, bool CLEAN>
+template <int D, bool CLEAN, bool DIAG>
 void flux_at(const Geom<double>& G, const State<double>& S, const Consts<double>& c, double* F) {
-  flux_of<D, CLEAN, false>(G, S, c, F);
+  flux_of<D, CLEAN, DIAG>(G, S, c, F);
 }
 
-template <int D>
+template <int D, bool DIAG>
 void speeds_at(const Geom<double>& G, const State<double>& S, const Consts<double>& c, double* lam,
                double* lam_q) {
   double lm, lp;
-  speeds_of<D, false>(G, S, cms2_of(S, c), lm, lp);
+  speeds_of<D, DIAG>(G, S, cms2_of(S, c), lm, lp);
   lam[0] = lm;
   lam[1] = lp;
   // the FP64 path's form: w(w + b^2) times the quadratic, halved linear coefficient
   double A, b, sq;
-  speed_quadratic<D, false>(G, S, c, A, b, sq);
+  speed_quadratic<D, DIAG>(G, S, c, A, b, sq);
   lam_q[0] = (-b - sq) / A;
   lam_q[1] = (-b + sq) / A;
 }
 
-}  // namespace
-
-extern "C" {
-
-void dev_prim2cons(long n, double gamma, int clean, const double* met, const double* prim,
-                   double* cons) {
+template <bool DIAG>
+void prim2cons_t(long n, double gamma, int clean, const double* met, const double* prim, double* cons) {
   const Consts<double> c = consts(gamma, 0.0);
   for (long i = 0; i < n; ++i) {
-    const Geom<double> G = make_geom<false>(met + 10 * i);
+    const Geom<double> G = make_geom<DIAG>(met + 10 * i);
     double P[9];
     for (int f = 0; f < 9; ++f) P[f] = prim[9 * i + f];
     if (!clean) P[8] = 0.0;
-    const State<double> S = make_state<false>(G, P, c);
+    const State<double> S = make_state<DIAG>(G, P, c);
     if (clean) cons_of<true>(G, S, cons + 9 * i);
     else {
       cons_of<false>(G, S, cons + 9 * i);
@@ -58,55 +54,87 @@ void dev_prim2cons(long n, double gamma, int clean, const double* met, const dou
   }
 }
 
-void dev_flux(long n, double gamma, double ch, int clean, int d, const double* met,
-              const double* prim, double* F) {
+template <bool DIAG>
+void flux_t(long n, double gamma, double ch, int clean, int d, const double* met, const double* prim,
+            double* F) {
   const Consts<double> c = consts(gamma, ch);
   for (long i = 0; i < n; ++i) {
-    const Geom<double> G = make_geom<false>(met + 10 * i);
+    const Geom<double> G = make_geom<DIAG>(met + 10 * i);
     double P[9];
     for (int f = 0; f < 9; ++f) P[f] = prim[9 * i + f];
     if (!clean) P[8] = 0.0;
-    const State<double> S = make_state<false>(G, P, c);
+    const State<double> S = make_state<DIAG>(G, P, c);
     double* o = F + 9 * i;
     o[8] = 0.0;
     if (clean) {
-      if (d == 0) flux_at<0, true>(G, S, c, o);
-      else if (d == 1) flux_at<1, true>(G, S, c, o);
-      else flux_at<2, true>(G, S, c, o);
+      if (d == 0) flux_at<0, true, DIAG>(G, S, c, o);
+      else if (d == 1) flux_at<1, true, DIAG>(G, S, c, o);
+      else flux_at<2, true, DIAG>(G, S, c, o);
     } else {
-      if (d == 0) flux_at<0, false>(G, S, c, o);
-      else if (d == 1) flux_at<1, false>(G, S, c, o);
-      else flux_at<2, false>(G, S, c, o);
+      if (d == 0) flux_at<0, false, DIAG>(G, S, c, o);
+      else if (d == 1) flux_at<1, false, DIAG>(G, S, c, o);
+      else flux_at<2, false, DIAG>(G, S, c, o);
     }
   }
 }
 
-void dev_speeds(long n, double gamma, int d, const double* met, const double* prim, double* lam,
-                double* lam_q) {
+template <bool DIAG>
+void speeds_t(long n, double gamma, int d, const double* met, const double* prim, double* lam,
+              double* lam_q) {
   const Consts<double> c = consts(gamma, 0.0);
   for (long i = 0; i < n; ++i) {
-    const Geom<double> G = make_geom<false>(met + 10 * i);
-    const State<double> S = make_state<false>(G, prim + 9 * i, c);
-    if (d == 0) speeds_at<0>(G, S, c, lam + 2 * i, lam_q + 2 * i);
-    else if (d == 1) speeds_at<1>(G, S, c, lam + 2 * i, lam_q + 2 * i);
-    else speeds_at<2>(G, S, c, lam + 2 * i, lam_q + 2 * i);
+    const Geom<double> G = make_geom<DIAG>(met + 10 * i);
+    const State<double> S = make_state<DIAG>(G, prim + 9 * i, c);
+    if (d == 0) speeds_at<0, DIAG>(G, S, c, lam + 2 * i, lam_q + 2 * i);
+    else if (d == 1) speeds_at<1, DIAG>(G, S, c, lam + 2 * i, lam_q + 2 * i);
+    else speeds_at<2, DIAG>(G, S, c, lam + 2 * i, lam_q + 2 * i);
   }
+}
+
+template <bool DIAG>
+void con2prim_t(long n, double gamma, int clean, const double* met, const double* cons,
+                const double* guess, double tol, int maxit, double* prim, int* status) {
+  const Consts<double> c = consts(gamma, 0.0);
+  for (long i = 0; i < n; ++i) {
+    const Geom<double> G = make_geom<DIAG>(met + 10 * i);
+    double P[9];
+    C2PResult r;
+    if (clean) r = con2prim<true, DIAG>(G, cons + 9 * i, guess + 9 * i, c, maxit, 0.01 * std::sqrt(tol), P);
+    else r = con2prim<false, DIAG>(G, cons + 9 * i, guess + 9 * i, c, maxit, 0.01 * std::sqrt(tol), P);
+    for (int f = 0; f < 9; ++f) prim[9 * i + f] = P[f];
+    status[i] = r.ok ? 0 : 1;
+  }
+}
+
+}  // namespace
+
+// diag = 1: the specialisation for zero shift and diagonal gamma (the metric must be such).
+extern "C" {
+
+void dev_prim2cons(long n, double gamma, int clean, int diag, const double* met, const double* prim,
+                   double* cons) {
+  if (diag) prim2cons_t<true>(n, gamma, clean, met, prim, cons);
+  else prim2cons_t<false>(n, gamma, clean, met, prim, cons);
+}
+
+void dev_flux(long n, double gamma, double ch, int clean, int diag, int d, const double* met,
+              const double* prim, double* F) {
+  if (diag) flux_t<true>(n, gamma, ch, clean, d, met, prim, F);
+  else flux_t<false>(n, gamma, ch, clean, d, met, prim, F);
+}
+
+void dev_speeds(long n, double gamma, int diag, int d, const double* met, const double* prim,
+                double* lam, double* lam_q) {
+  if (diag) speeds_t<true>(n, gamma, d, met, prim, lam, lam_q);
+  else speeds_t<false>(n, gamma, d, met, prim, lam, lam_q);
 }
 
 // Recovery (the 2D Newton with its FP32 start and bracketed fallback) from the conserved
 // vector and a guess; status[i] = 1 when it failed.
-void dev_con2prim(long n, double gamma, int clean, const double* met, const double* cons,
+void dev_con2prim(long n, double gamma, int clean, int diag, const double* met, const double* cons,
                   const double* guess, double tol, int maxit, double* prim, int* status) {
-  const Consts<double> c = consts(gamma, 0.0);
-  for (long i = 0; i < n; ++i) {
-    const Geom<double> G = make_geom<false>(met + 10 * i);
-    double P[9];
-    C2PResult r;
-    if (clean) r = con2prim<true, false>(G, cons + 9 * i, guess + 9 * i, c, maxit, 0.01 * std::sqrt(tol), P);
-    else r = con2prim<false, false>(G, cons + 9 * i, guess + 9 * i, c, maxit, 0.01 * std::sqrt(tol), P);
-    for (int f = 0; f < 9; ++f) prim[9 * i + f] = P[f];
-    status[i] = r.ok ? 0 : 1;
-  }
+  if (diag) con2prim_t<true>(n, gamma, clean, met, cons, guess, tol, maxit, prim, status);
+  else con2prim_t<false>(n, gamma, clean, met, cons, guess, tol, maxit, prim, status);
 }
 
 }  // extern "C"

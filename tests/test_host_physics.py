@@ -1,7 +1,8 @@
 """The CUDA path's pointwise physics (hzn_physics.cuh: metric geometry, state algebra, conserved
 and flux vectors, wave speeds in both the plain and the FP64 kernel's scaled form, and the
 recovery) built for the host and compared with the oracle's pointwise functions on random
-states of high Lorentz factor and magnetisation in random general 3+1 metrics.  CPU only: the
+states of high Lorentz factor and magnetisation, in random general 3+1 metrics and in their
+diagonal, zero-shift reductions through the kernels' DIAG specialisation.  CPU only: the
 same device templates, no GPU."""
 import ctypes
 import os
@@ -30,12 +31,12 @@ def dev():
     subprocess.run(cmd, check=True)
     L = ctypes.CDLL(out)
     dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
-    L.dev_prim2cons.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_int, dp, dp, dp]
-    L.dev_flux.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                           ctypes.c_int, dp, dp, dp]
-    L.dev_speeds.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp]
-    L.dev_con2prim.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_int, dp, dp, dp,
-                               ctypes.c_double, ctypes.c_int, dp, ip]
+    ci = ctypes.c_int
+    L.dev_prim2cons.argtypes = [ctypes.c_long, ctypes.c_double, ci, ci, dp, dp, dp]
+    L.dev_flux.argtypes = [ctypes.c_long, ctypes.c_double, ctypes.c_double, ci, ci, ci, dp, dp, dp]
+    L.dev_speeds.argtypes = [ctypes.c_long, ctypes.c_double, ci, ci, dp, dp, dp, dp]
+    L.dev_con2prim.argtypes = [ctypes.c_long, ctypes.c_double, ci, ci, dp, dp, dp,
+                               ctypes.c_double, ci, dp, ip]
     for f in (L.dev_prim2cons, L.dev_flux, L.dev_speeds, L.dev_con2prim):
         f.restype = None
     return L
@@ -45,12 +46,19 @@ def _p(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-@pytest.fixture(scope="module")
-def states():
-    met = np.ascontiguousarray(W.random_metric_points(N, seed=71))
+@pytest.fixture(scope="module", params=[0, 1], ids=["general", "diag"])
+def states(request):
+    """(diag, met, prim): general 3+1 metrics, or the same with zero shift and diagonal gamma
+    (the kernels' DIAG specialisation)."""
+    diag = request.param
+    met = W.random_metric_points(N, seed=71)
+    if diag:
+        met[:, 1:4] = 0.0
+        met[:, [5, 6, 8]] = 0.0
+    met = np.ascontiguousarray(met)
     prim = np.ascontiguousarray(W.random_prim_points(N, seed=72, met=met, wmax=10.0, sigma_max=100.0))
     prim[:, 8] = np.random.Generator(np.random.PCG64(73)).uniform(-0.05, 0.05, N)
-    return met, prim
+    return diag, met, prim
 
 
 def _rel(a, b):
@@ -61,9 +69,9 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("clean", [0, 1])
 def test_conserved_vector_matches_oracle(dev, states, clean):
-    met, prim = states
+    diag, met, prim = states
     got = np.zeros((N, 9))
-    dev.dev_prim2cons(N, GAMMA, clean, _p(met), _p(prim), _p(got))
+    dev.dev_prim2cons(N, GAMMA, clean, diag, _p(met), _p(prim), _p(got))
     want = O.prim2cons(O.make_opts(GAMMA, cleaning=bool(clean)), met, prim)
     cols = slice(0, 9 if clean else 8)
     assert _rel(got[:, cols], want[:, cols]) < 5e-12
@@ -72,9 +80,9 @@ def test_conserved_vector_matches_oracle(dev, states, clean):
 @pytest.mark.parametrize("clean", [0, 1])
 @pytest.mark.parametrize("d", [0, 1, 2])
 def test_flux_vector_matches_oracle(dev, states, clean, d):
-    met, prim = states
+    diag, met, prim = states
     got = np.zeros((N, 9))
-    dev.dev_flux(N, GAMMA, CH, clean, d, _p(met), _p(prim), _p(got))
+    dev.dev_flux(N, GAMMA, CH, clean, diag, d, _p(met), _p(prim), _p(got))
     want = O.flux(O.make_opts(GAMMA, cleaning=bool(clean), ch=CH), d, met, prim)
     cols = slice(0, 9 if clean else 8)
     assert _rel(got[:, cols], want[:, cols]) < 5e-12  # measured <= 9e-13 (W <= 10, b^2/rho <= 100)
@@ -84,10 +92,10 @@ def test_flux_vector_matches_oracle(dev, states, clean, d):
 def test_wave_speeds_both_forms_match_oracle(dev, states, d):
     """The plain quadratic (mixed and pair paths) and the FP64 kernel's form (multiplied through
     by w(w + b^2), halved linear coefficient) give the oracle's speeds."""
-    met, prim = states
+    diag, met, prim = states
     lam = np.zeros((N, 2))
     lam_q = np.zeros((N, 2))
-    dev.dev_speeds(N, GAMMA, d, _p(met), _p(prim), _p(lam), _p(lam_q))
+    dev.dev_speeds(N, GAMMA, diag, d, _p(met), _p(prim), _p(lam), _p(lam_q))
     want = O.speeds(O.make_opts(GAMMA), d, met, prim)
     assert np.abs(lam - want).max() < 1e-12
     assert np.abs(lam_q - want).max() < 1e-12
@@ -97,7 +105,7 @@ def test_wave_speeds_both_forms_match_oracle(dev, states, d):
 def test_recovery_returns_the_state_and_matches_oracle(dev, states):
     """From the conserved vector of each state and a guess 10 % off, the device recovery returns
     the state (round trip) and the oracle's root."""
-    met, prim = states
+    diag, met, prim = states
     cons = O.prim2cons(O.make_opts(GAMMA, cleaning=True), met, prim)
     guess = prim.copy()
     guess[:, 0] *= 1.1
@@ -105,7 +113,7 @@ def test_recovery_returns_the_state_and_matches_oracle(dev, states):
     guess[:, 2:5] *= 0.95
     got = np.zeros((N, 9))
     status = np.zeros(N, dtype=np.int32)
-    dev.dev_con2prim(N, GAMMA, 1, _p(met), _p(cons), _p(guess), 1e-12, 50, _p(got),
+    dev.dev_con2prim(N, GAMMA, 1, diag, _p(met), _p(cons), _p(guess), 1e-12, 50, _p(got),
                      status.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     assert np.all(status == 0)
     assert _rel(got, prim) < 1e-11  # measured 2.7e-13
