@@ -137,4 +137,24 @@ void dev_con2prim(long n, double gamma, int clean, int diag, const double* met, 
   else con2prim_t<false>(n, gamma, clean, met, cons, guess, tol, maxit, prim, status);
 }
 
+// Face states of a 1-D array at the faces between cells c-1 and c, c = 3 .. n-3 (as the
+// oracle's reconstruct_1d): recon 0 MC (FP64), 1 PPM (FP64), 2 MC in double-word arithmetic
+// (split inputs, result widened).
+void dev_reconstruct(int recon, long n, const double* q, double* left, double* right) {
+  for (long c = 3; c + 2 < n; ++c) {
+    const double* v = q + c - 3;
+    if (recon == 1) {
+      ppm_face<double>(v[0], v[1], v[2], v[3], v[4], v[5], left[c], right[c]);
+    } else if (recon == 0) {
+      left[c] = v[2] + mc_half_slope(v[2] - v[1], v[3] - v[2]);
+      right[c] = v[3] - mc_half_slope(v[3] - v[2], v[4] - v[3]);
+    } else {
+      const f32x2 a = dw::split(v[1]), b = dw::split(v[2]), cc = dw::split(v[3]), d = dw::split(v[4]);
+      const f32x2 l = b + mc_half_slope(b - a, cc - b), r = cc - mc_half_slope(cc - b, d - cc);
+      left[c] = (double)l.hi + (double)l.lo;
+      right[c] = (double)r.hi + (double)r.lo;
+    }
+  }
+}
+
 }  // extern "C"

@@ -37,7 +37,8 @@ def dev():
     L.dev_speeds.argtypes = [ctypes.c_long, ctypes.c_double, ci, ci, dp, dp, dp, dp]
     L.dev_con2prim.argtypes = [ctypes.c_long, ctypes.c_double, ci, ci, dp, dp, dp,
                                ctypes.c_double, ci, dp, ip]
-    for f in (L.dev_prim2cons, L.dev_flux, L.dev_speeds, L.dev_con2prim):
+    L.dev_reconstruct.argtypes = [ci, ctypes.c_long, dp, dp, dp]
+    for f in (L.dev_prim2cons, L.dev_flux, L.dev_speeds, L.dev_con2prim, L.dev_reconstruct):
         f.restype = None
     return L
 
@@ -119,3 +120,41 @@ def test_recovery_returns_the_state_and_matches_oracle(dev, states):
     assert _rel(got, prim) < 1e-11  # measured 2.7e-13
     orc, _, _ = O.cons2prim(O.make_opts(GAMMA, cleaning=True), met, cons, guess)
     assert _rel(got, orc) < 1e-11
+
+
+def _profiles():
+    """1-D arrays with smooth parts, jumps, plateaus (exact zero differences), isolated extrema
+    and values spanning many decades."""
+    rng = np.random.Generator(np.random.PCG64(74))
+    x = np.linspace(0.0, 1.0, 400)
+    out = [np.sin(7 * x) + 0.3 * np.cos(31 * x),
+           np.where(x < 0.4, 1.0, 0.125) + np.where(x > 0.7, 2.0, 0.0),
+           np.round(rng.uniform(0, 4, 400)) * 0.25,
+           10.0 ** rng.uniform(-12, 2, 400),
+           np.exp(-((x - 0.5) / 0.05) ** 2)]
+    return [np.ascontiguousarray(q) for q in out]
+
+
+def test_mc_reconstruction_is_the_oracles_bit_for_bit(dev):
+    """The FP64 MC faces (bit-pattern minimum, exponent-arithmetic quarter) are the numbers of
+    the oracle's floating-point MC, exactly."""
+    for q in _profiles():
+        n = len(q)
+        left, right = np.full(n, np.nan), np.full(n, np.nan)
+        dev.dev_reconstruct(0, n, _p(q), _p(left), _p(right))
+        wl, wr = O.reconstruct_1d(O.RECON_MC, q)
+        assert np.array_equal(left[3:n - 2], wl[3:n - 2]) and np.array_equal(right[3:n - 2], wr[3:n - 2])
+
+
+def test_ppm_and_pair_mc_reconstruction_match_oracle(dev):
+    for q in _profiles():
+        n = len(q)
+        scale = np.abs(q).max()
+        left, right = np.full(n, np.nan), np.full(n, np.nan)
+        dev.dev_reconstruct(1, n, _p(q), _p(left), _p(right))
+        wl, wr = O.reconstruct_1d(O.RECON_PPM, q)
+        s = slice(3, n - 2)
+        assert np.abs(left[s] - wl[s]).max() <= 1e-14 * scale and np.abs(right[s] - wr[s]).max() <= 1e-14 * scale
+        dev.dev_reconstruct(2, n, _p(q), _p(left), _p(right))
+        wl, wr = O.reconstruct_1d(O.RECON_MC, q)
+        assert np.abs(left[s] - wl[s]).max() <= 1e-13 * scale and np.abs(right[s] - wr[s]).max() <= 1e-13 * scale
