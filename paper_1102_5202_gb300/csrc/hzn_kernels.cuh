@@ -402,12 +402,6 @@ __device__ __forceinline__ void face_flux_dw(const KParams& kp, const double* __
   for (int f = 0; f < NV; ++f) out[f * ostride] = F[f];
 }
 
-// Centre 4-metric quantities used by the source: g_tt, beta_i, gamma_ij at one cell.
-template <typename R>
-struct G4 {
-  R gtt, blx, bly, blz, gxx, gxy, gxz, gyy, gyz, gzz;
-};
-
 template <bool DIAG, typename R, typename S>
 __device__ __forceinline__ G4<R> g4_at(const KParams& kp, const S* __restrict__ M, long long off) {
   R m[10];
@@ -429,51 +423,6 @@ __device__ __forceinline__ G4<R> g4_at(const KParams& kp, const S* __restrict__ 
     g.gtt = -m[M_ALP] * m[M_ALP] + (g.blx * m[M_BX] + g.bly * m[M_BY] + g.blz * m[M_BZ]);
   }
   return g;
-}
-
-// Contravariant stress-energy T^{ab} = (w + b^2) u^a u^b + (p + b^2/2) g^{ab} - b^a b^b.
-template <typename R>
-struct Tup {
-  R tt, tx, ty, tz, xx, xy, xz, yy, yz, zz;
-};
-
-template <bool DIAG, typename R>
-__device__ __forceinline__ Tup<R> tup_of(const Geom<R>& G, const State<R>& S) {
-  const R wt = S.w + S.b2, pt = S.p + R(0.5) * S.b2;
-  const R ia2 = G.ialp * G.ialp;
-  Tup<R> T;
-  T.tt = wt * S.ut * S.ut - pt * ia2 - S.bt * S.bt;
-  if constexpr (DIAG) {
-    T.tx = wt * S.ut * S.ux - S.bt * S.bx;
-    T.ty = wt * S.ut * S.uy - S.bt * S.by;
-    T.tz = wt * S.ut * S.uz - S.bt * S.bz;
-    T.xx = wt * S.ux * S.ux + pt * G.ixx - S.bx * S.bx;
-    T.yy = wt * S.uy * S.uy + pt * G.iyy - S.by * S.by;
-    T.zz = wt * S.uz * S.uz + pt * G.izz - S.bz * S.bz;
-    T.xy = T.xz = T.yz = R(0);  // multiplied by identically zero metric derivatives
-  } else {
-    T.tx = wt * S.ut * S.ux + pt * G.bx * ia2 - S.bt * S.bx;
-    T.ty = wt * S.ut * S.uy + pt * G.by * ia2 - S.bt * S.by;
-    T.tz = wt * S.ut * S.uz + pt * G.bz * ia2 - S.bt * S.bz;
-    T.xx = wt * S.ux * S.ux + pt * (G.ixx - G.bx * G.bx * ia2) - S.bx * S.bx;
-    T.xy = wt * S.ux * S.uy + pt * (G.ixy - G.bx * G.by * ia2) - S.bx * S.by;
-    T.xz = wt * S.ux * S.uz + pt * (G.ixz - G.bx * G.bz * ia2) - S.bx * S.bz;
-    T.yy = wt * S.uy * S.uy + pt * (G.iyy - G.by * G.by * ia2) - S.by * S.by;
-    T.yz = wt * S.uy * S.uz + pt * (G.iyz - G.by * G.bz * ia2) - S.by * S.bz;
-    T.zz = wt * S.uz * S.uz + pt * (G.izz - G.bz * G.bz * ia2) - S.bz * S.bz;
-  }
-  return T;
-}
-
-// T^{ab} (g_ab(+) - g_ab(-)) between the neighbours gp and gm (unscaled centred difference).
-template <bool DIAG, typename R>
-__device__ __forceinline__ R tdg(const Tup<R>& T, const G4<R>& gp, const G4<R>& gm) {
-  R s = T.tt * (gp.gtt - gm.gtt) + T.xx * (gp.gxx - gm.gxx) + T.yy * (gp.gyy - gm.gyy) +
-        T.zz * (gp.gzz - gm.gzz);
-  if constexpr (!DIAG)
-    s += R(2) * (T.tx * (gp.blx - gm.blx) + T.ty * (gp.bly - gm.bly) + T.tz * (gp.blz - gm.blz) +
-                 T.xy * (gp.gxy - gm.gxy) + T.xz * (gp.gxz - gm.gxz) + T.yz * (gp.gyz - gm.gyz));
-  return s;
 }
 
 // max over active axes of max|lambda| / dx at a cell centre (plus the cleaning speed).

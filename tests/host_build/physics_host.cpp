@@ -137,6 +137,51 @@ void dev_con2prim(long n, double gamma, int clean, int diag, const double* met, 
   else con2prim_t<false>(n, gamma, clean, met, cons, guess, tol, maxit, prim, status);
 }
 
+}  // extern "C"
+
+// Metric source S_i = 1/2 sqrt(-g) T^{ab} d_i g_ab from the kernels' algebra (tup_of, tdg) for
+// given derivatives dg (n x 3 x 16, d_i g_ab row-major 4 x 4), as the oracle's
+// source_pointwise: the derivative enters as the difference of two neighbours g(+) = dg / 2,
+// g(-) = -dg / 2.  src n x 4 (S_t = 0, S_x, S_y, S_z).
+static G4<double> g4_of(const double* m, double f) {
+  G4<double> g;
+  g.gtt = f * m[0];
+  g.blx = f * m[1];
+  g.bly = f * m[2];
+  g.blz = f * m[3];
+  g.gxx = f * m[5];
+  g.gxy = f * m[6];
+  g.gxz = f * m[7];
+  g.gyy = f * m[10];
+  g.gyz = f * m[11];
+  g.gzz = f * m[15];
+  return g;
+}
+
+template <bool DIAG>
+static void source_t(long n, double gamma, const double* met, const double* dg, const double* prim,
+                     double* src) {
+  const Consts<double> c = consts(gamma, 0.0);
+  for (long i = 0; i < n; ++i) {
+    const Geom<double> G = make_geom<DIAG>(met + 10 * i);
+    const State<double> S = make_state<DIAG>(G, prim + 9 * i, c);
+    const Tup<double> T = tup_of<DIAG>(G, S);
+    src[4 * i] = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double* m = dg + 48 * i + 16 * d;
+      src[4 * i + 1 + d] = 0.5 * G.sqrtmg * tdg<DIAG>(T, g4_of(m, 0.5), g4_of(m, -0.5));
+    }
+  }
+}
+
+extern "C" void dev_source(long n, double gamma, int diag, const double* met, const double* dg,
+                           const double* prim, double* src) {
+  if (diag) source_t<true>(n, gamma, met, dg, prim, src);
+  else source_t<false>(n, gamma, met, dg, prim, src);
+}
+
+extern "C" {
+
 // Face states of a 1-D array at the faces between cells c-1 and c, c = 3 .. n-3 (as the
 // oracle's reconstruct_1d): recon 0 MC (FP64), 1 PPM (FP64), 2 MC in double-word arithmetic
 // (split inputs, result widened).

@@ -38,7 +38,8 @@ def dev():
     L.dev_con2prim.argtypes = [ctypes.c_long, ctypes.c_double, ci, ci, dp, dp, dp,
                                ctypes.c_double, ci, dp, ip]
     L.dev_reconstruct.argtypes = [ci, ctypes.c_long, dp, dp, dp]
-    for f in (L.dev_prim2cons, L.dev_flux, L.dev_speeds, L.dev_con2prim, L.dev_reconstruct):
+    L.dev_source.argtypes = [ctypes.c_long, ctypes.c_double, ci, dp, dp, dp, dp]
+    for f in (L.dev_prim2cons, L.dev_flux, L.dev_speeds, L.dev_con2prim, L.dev_reconstruct, L.dev_source):
         f.restype = None
     return L
 
@@ -120,6 +121,23 @@ def test_recovery_returns_the_state_and_matches_oracle(dev, states):
     assert _rel(got, prim) < 1e-11  # measured 2.7e-13
     orc, _, _ = O.cons2prim(O.make_opts(GAMMA, cleaning=True), met, cons, guess)
     assert _rel(got, orc) < 1e-11
+
+
+def test_metric_source_matches_oracle(dev, states):
+    """The kernels' source algebra (T^{ab} of tup_of contracted with metric differences by tdg)
+    against the oracle's 1/2 sqrt(-g) T^{ab} d_i g_ab, for random symmetric derivatives (diagonal
+    ones for the DIAG specialisation, whose metrics keep zero shift and diagonal gamma)."""
+    diag, met, prim = states
+    rng = np.random.Generator(np.random.PCG64(75))
+    dg = rng.uniform(-0.3, 0.3, (N, 3, 4, 4))
+    dg = 0.5 * (dg + dg.transpose(0, 1, 3, 2))
+    if diag:
+        dg = dg * np.eye(4)[None, None]
+    dg = np.ascontiguousarray(dg.reshape(N, 48))
+    got = np.zeros((N, 4))
+    dev.dev_source(N, GAMMA, diag, _p(met), _p(dg), _p(prim), _p(got))
+    want = O.source_pointwise(O.make_opts(GAMMA), met, dg, prim)
+    assert _rel(got, want) < 1e-12
 
 
 def _profiles():
