@@ -647,6 +647,7 @@ __device__ __forceinline__ void ift(const Geom<double>& G, const State<double>& 
   mu[8] = CLEAN ? lamP[8] * rcp_fast(G.sqrtg) : 0.0;
 }
 
+#ifdef __CUDACC__  // the kernels and their launchers (the reverse physics above also builds for the host)
 // One thread per face of every active axis: flux adjoint from lam_L, face reverse, store the
 // adjoints of the two reconstructed states.
 template <bool CLEAN, bool DIAG>
@@ -889,6 +890,8 @@ void adj_launch_face(bool clean, dim3 grid, int threads, cudaStream_t st, const 
   if (clean) k_adj_face<true, DIAG><<<grid, threads, 0, st>>>(kp, sh, P, M, bufs);
   else k_adj_face<false, DIAG><<<grid, threads, 0, st>>>(kp, sh, P, M, bufs);
 }
+
+#endif  // __CUDACC__
 
 }  // namespace adj
 }  // namespace hzn

@@ -31,3 +31,13 @@ inline int __double2loint(double d) { return (int)(unsigned)((unsigned long long
 inline double __hiloint2double(int hi, int lo) {
   return __longlong_as_double((long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned)lo));
 }
+
+// types the internal headers name in host declarations
+typedef struct CUstream_st* cudaStream_t;
+struct dim3 {
+  unsigned x, y, z;
+  dim3(unsigned a = 1, unsigned b = 1, unsigned c = 1) : x(a), y(b), z(c) {}
+};
+
+template <class T>
+inline T __ldg(const T* p) { return *p; }
