@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -122,7 +123,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $HZN_CLOCKS_DIR (default: the temporary directory)
+        self.path = os.path.join(os.environ.get("HZN_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"hzn_clocks_rank{index}.csv")
 
     def start(self):
         try:

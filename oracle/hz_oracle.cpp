@@ -13,7 +13,7 @@
 //   stage (§3.2) -> conservative-to-primitive recovery (§2.2 Newton-Raphson iteration, §3.2).
 // Every step runs over the whole grid before the next one starts: no fusion, no tiling.
 //
-// Readings of points where the paper is silent (each one listed in the design doc):
+// Readings of points where the paper is silent:
 //   * induction flux along i of sqrt(-g) B^j is sqrt(-g)(b^j u^i - b^i u^j), the sign that
 //     follows from the dual Maxwell equation with B^i = *F^{it} (§2.1 Eq. 1-2);
 //   * RK3 is the Shu-Osher strong-stability-preserving scheme;
