@@ -457,6 +457,7 @@ __device__ __forceinline__ double cell_max_speed(const KParams& kp, const Geom<R
   return v;
 }
 
+#ifdef __CUDACC__  // device-only: block reduction, kernels, launchers (the helpers build for the host too)
 // Block reduction of the CFL maximum, the failure count and the largest iteration count.
 template <int NT>
 __device__ __forceinline__ void block_stats(DevScalars* sc, double vloc, int nfail, int maxit,
@@ -488,6 +489,7 @@ __device__ __forceinline__ void block_stats(DevScalars* sc, double vloc, int nfa
     if (mi) atomicMax(&sc->maxit, mi);
   }
 }
+#endif  // __CUDACC__
 
 // Recovery with atmosphere / floor handling; rewrites U when the cell is reset.  TG, TP: the
 // element types of the guess and of the result (float for the mixed path, whose primitive
@@ -528,6 +530,7 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
   return r.ok ? 0 : 1;
 }
 
+#ifdef __CUDACC__
 // PAIR (FP64 state only): reconstruction, face states, fluxes, HLLE, divergence and sources in
 // double-word arithmetic (f32x2, on the FP32 pipes); the RK update, the recovery and the CFL
 // maximum in FP64 as on the FP64 path.
@@ -924,5 +927,7 @@ void launch_prim2cons_t(const Variant& v, const KParams& kp, const void* Pv, con
     else k_prim2cons<false, false, MIXED><<<nb, 256, 0, st>>>(kp, P, M, U);
   }
 }
+
+#endif  // __CUDACC__
 
 }  // namespace hzn
