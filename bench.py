@@ -38,9 +38,23 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA throughput measured on this machine's GB300 with an in-register DFMA loop
 # (profiles/fp64_alu_peak.md): 2 DFMA per clock per SM x 152 SMs.
 FP64_PEAK_TFLOPS = 1.194
+FP32_PEAK_TFLOPS = 72.98  # FFMA loop of the same probe, 8 blocks per SM
+# Algorithmic flops per zone update (one cell, one RK3 step) of the method on the blob
+# workload at 192^3 (MC, cleaning on, CFL 0.5), from the op-counting oracle
+# (oracle/opcount_blob3d.json, written by oracle/write_counts.py): the floating-point operations
+# (+, -, *, /, sqrt) that each face's and each cell's results and decisions depend on, each
+# counted once, operations on structural zeros of the diagonal spacetime and the static
+# geometry excluded.  The roofline's achieved rate is this count over the measured time.
+FP64_ALG_FLOPS_PER_ZU = 3899.1264114379883
+# The part of it in the phases the mixed path keeps in FP64 (RK update, recovery, CFL maximum);
+# the rest (reconstruction, face states, fluxes, speeds, HLLE, divergence, sources) runs in FP32
+# there.
+ALG_FLOPS_PER_ZU_FP64_PHASES = 308.9395263106735
 # FP64 operations per cell per substep executed by the fused substep kernel (3-D, cleaning
 # on, diagonal metric with its geometry tables), from ncu instruction counters on the 128^3
-# blob (profiles/k_substep_blob3d.md): DFMA counted as 2 flops, DADD/DMUL as 1.
+# blob (profiles/k_substep_blob3d.md): DFMA counted as 2 flops, DADD/DMUL as 1.  Reported
+# beside the algorithmic rate: the kernel's own arithmetic (reciprocal refinements, the
+# two-dimensional Newton recovery) differs from the method's count.
 FP64_FLOPS_PER_CELL_SUBSTEP = 1803.9
 # FP64 instructions (DFMA + DMUL + DADD) per cell per substep from the same capture, and the
 # FP64 instruction rate of the pipe measured by the probe (1.91 DFMA per clock per SM at
@@ -218,12 +232,16 @@ def run_gpu(args, rank, world, local):
 
     # roofline of the dominant kernel (the fused substep): three launches per step
     substep_s = statistics.mean(step_ms) * 1e-3 / 3.0
-    if FP64_FLOPS_PER_CELL_SUBSTEP:
-        ach = FP64_FLOPS_PER_CELL_SUBSTEP * cells / substep_s / 1e12
+    if FP64_ALG_FLOPS_PER_ZU:
+        ach = FP64_ALG_FLOPS_PER_ZU / 3.0 * cells / substep_s / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": DRAM_BYTES_PER_CELL_SUBSTEP * cells if DRAM_BYTES_PER_CELL_SUBSTEP else None,
-                "kernel": "k_substep<32,4,3-D,cleaning,diag,FP64,MC>", "peak_source": "measured FP64 DFMA loop"}
+                "kernel": "k_substep<32,4,3-D,cleaning,diag,FP64,MC>", "peak_source": "measured FP64 DFMA loop",
+                "algorithmic_flops_per_zu": FP64_ALG_FLOPS_PER_ZU}
+        impl = FP64_FLOPS_PER_CELL_SUBSTEP * cells / substep_s / 1e12
+        roof["implemented_fp64_flops"] = {"per_cell_substep": FP64_FLOPS_PER_CELL_SUBSTEP, "achieved": impl,
+                                          "frac": impl / FP64_PEAK_TFLOPS}
         inst = FP64_INST_PER_CELL_SUBSTEP * cells / substep_s
         roof["fp64_instructions"] = {"per_cell_substep": FP64_INST_PER_CELL_SUBSTEP, "achieved_per_s": inst,
                                      "peak_per_s": FP64_INST_PEAK_PER_S, "frac": inst / FP64_INST_PEAK_PER_S}
@@ -325,7 +343,9 @@ def run_mixed(args, dist, local, hbm_peak):
     value = units / seconds
     ach = HBM_BYTES_PER_ZU_MIXED * value / world_size(dist) / 1e9
     substep_s = sec / args.steps / 3.0
-    fl = MIXED_FP64_FLOPS_PER_CELL_SUBSTEP * P.ncell / substep_s / 1e12
+    fl = ALG_FLOPS_PER_ZU_FP64_PHASES / 3.0 * P.ncell / substep_s / 1e12
+    fl32 = (FP64_ALG_FLOPS_PER_ZU - ALG_FLOPS_PER_ZU_FP64_PHASES) / 3.0 * P.ncell / substep_s / 1e12
+    impl = MIXED_FP64_FLOPS_PER_CELL_SUBSTEP * P.ncell / substep_s / 1e12
     del s
     torch.cuda.empty_cache()
     err = mixed_error(P) if args.mixed_error else None
@@ -336,7 +356,12 @@ def run_mixed(args, dist, local, hbm_peak):
                          "frac": fl / FP64_PEAK_TFLOPS,
                          "traffic": (MIXED_DRAM_BYTES_PER_CELL_SUBSTEP * P.ncell
                                      if MIXED_DRAM_BYTES_PER_CELL_SUBSTEP else None),
-                         "kernel": "k_substep<32,4,3-D,cleaning,diag,mixed> (FP64 recovery and update)"},
+                         "kernel": "k_substep<32,4,3-D,cleaning,diag,mixed> (FP64 recovery and update)",
+                         "algorithmic_flops_per_zu_fp64_phases": ALG_FLOPS_PER_ZU_FP64_PHASES,
+                         "implemented_fp64_flops": {"per_cell_substep": MIXED_FP64_FLOPS_PER_CELL_SUBSTEP,
+                                                    "achieved": impl, "frac": impl / FP64_PEAK_TFLOPS},
+                         "fp32_phases": {"achieved": fl32, "peak": FP32_PEAK_TFLOPS,
+                                         "frac": fl32 / FP32_PEAK_TFLOPS}},
             "hbm_roofline": {"bytes_per_zu": HBM_BYTES_PER_ZU_MIXED, "achieved": ach, "peak": hbm_peak,
                              "unit": "GB/s", "frac": ach / hbm_peak,
                              "roofline_zu_per_s": hbm_peak * 1e9 / HBM_BYTES_PER_ZU_MIXED},
