@@ -5,7 +5,8 @@
 // the metric source and the cleaning damping are formed here in the order the substep kernel
 // uses.  Arrays in the oracle's layouts: met (10, nz+2gz, ny+2gy, nx+2gx), prim and out
 // (9, nz, ny, nx); inside, odd pitches and field strides with NaN padding, so that a read outside
-// the stencil or a wrong stride shows in the result.
+// the stencil or a wrong stride shows in the result.  Also the recovery with the atmosphere and
+// floor rules (recover) and the CFL maximum (cell_max_speed) of the same header.
 #include <cmath>
 #include <limits>
 #include <vector>
@@ -243,4 +244,86 @@ extern "C" int dev_rhs(const int* n, const double* dx, const int* bc, double gam
   HZ_RHS_MIXED(0, 0, 1) HZ_RHS_MIXED(0, 1, 1) HZ_RHS_MIXED(1, 0, 1) HZ_RHS_MIXED(1, 1, 1)
 #undef HZ_RHS_MIXED
   return 1;
+}
+
+// Recovery of n pointwise states with the kernels' atmosphere and floor rules (recover in
+// hzn_kernels.cuh): met n x 10, cons n x 9 (rewritten where a cell is reset), guess and prim
+// n x 9; status[i] = 1 where the root solve failed.  p_atm: the atmosphere pressure.
+extern "C" void dev_recover(long n, double gamma, int clean, int diag, double rho_floor, double p_floor,
+                            double p_atm, double rho_atm, int maxit, double tol, const double* met,
+                            double* cons, const double* guess, double* prim, int* status) {
+  KParams kp = KParams{};
+  kp.gamma = gamma;
+  kp.gfac = gamma / (gamma - 1.0);
+  kp.rho_floor = rho_floor;
+  kp.p_floor = p_floor;
+  kp.p_atm = p_atm;
+  kp.rho_atm = rho_atm;
+  kp.c2p_maxit = maxit;
+  kp.c2p_tol = tol;
+  kp.c2p_step_tol = 0.01 * std::sqrt(tol);
+  const Consts<double> c = consts_of<double>(kp);
+  for (long q = 0; q < n; ++q) {
+    double* U = cons + 9 * q;
+    double Pg[9], P[9];
+    for (int f = 0; f < 9; ++f) Pg[f] = guess[9 * q + f];
+    if (!clean) {
+      Pg[8] = 0.0;
+      U[8] = 0.0;
+    }
+    int it = 0;
+    if (diag) {
+      const Geom<double> G = make_geom<true>(met + 10 * q);
+      status[q] = clean ? recover<true, true>(kp, G, U, Pg, c, P, it) : recover<false, true>(kp, G, U, Pg, c, P, it);
+    } else {
+      const Geom<double> G = make_geom<false>(met + 10 * q);
+      status[q] = clean ? recover<true, false>(kp, G, U, Pg, c, P, it) : recover<false, false>(kp, G, U, Pg, c, P, it);
+    }
+    for (int f = 0; f < 9; ++f) prim[9 * q + f] = P[f];
+  }
+}
+
+namespace {
+
+template <bool YA, bool ZA, bool CLEAN, bool DIAG>
+double max_speed_t(const Host& h) {
+  const KParams& kp = h.kp;
+  const Consts<double> c = consts_of<double>(kp);
+  double v = 0.0;
+  for (int k = 0; k < kp.nz; ++k)
+    for (int j = 0; j < kp.ny; ++j)
+      for (int i = 0; i < kp.nx; ++i) {
+        const long long off = (long long)k * kp.plane + (long long)j * kp.pitch + i;
+        Geom<double> G;
+        if constexpr (DIAG) {
+          G = geo_load<double>(kp.geo_c, met_off(kp, i, j, k), kp.ms);
+        } else {
+          double m[10];
+          load_metric<DIAG>(kp, h.M.data(), met_off(kp, i, j, k), m);
+          G = make_geom<DIAG>(m);
+        }
+        double P[9];
+        for (int f = 0; f < 9; ++f) P[f] = h.P[f * kp.fs + off];
+        if (!CLEAN) P[8] = 0.0;
+        v = std::fmax(v, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, P, c));
+      }
+  return v;
+}
+
+}  // namespace
+
+// The CFL maximum over the grid, max over cells and active axes of max |lambda| / dx (with the
+// cleaning speed when on), from the kernels' cell_max_speed; layouts as dev_rhs.
+extern "C" double dev_max_speed(const int* n, const double* dx, const int* bc, double gamma, int clean,
+                                double ch, int diag, const double* met, const double* prim) {
+  Host h;
+  setup(h, n, dx, bc, gamma, clean, ch, 0.0, met, prim);
+  const bool ya = n[1] > 1, za = n[2] > 1;
+#define HZ_MS(Y, Z, C, D) \
+  if (ya == Y && za == Z && clean == C && diag == D) return max_speed_t<Y, Z, C, D>(h);
+  HZ_MS(false, false, 0, 0) HZ_MS(false, false, 0, 1) HZ_MS(false, false, 1, 0) HZ_MS(false, false, 1, 1)
+  HZ_MS(true, false, 0, 0) HZ_MS(true, false, 0, 1) HZ_MS(true, false, 1, 0) HZ_MS(true, false, 1, 1)
+  HZ_MS(true, true, 0, 0) HZ_MS(true, true, 0, 1) HZ_MS(true, true, 1, 0) HZ_MS(true, true, 1, 1)
+#undef HZ_MS
+  return -1.0;
 }

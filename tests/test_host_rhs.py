@@ -6,7 +6,9 @@ geometry tables, and compared with the oracle's `rhs` field by field on small gr
 diagonal-metric star, smooth periodic data in a general metric (shift, non-diagonal gamma) in
 2-D and 3-D with a non-zero cleaning scalar, and a discontinuous shock tube along each axis.
 CPU only: the same device templates, no GPU.  The harness pads the arrays with NaN and uses odd
-pitches, so a read outside the stencil or a wrong stride fails here."""
+pitches, so a read outside the stencil or a wrong stride fails here.  Also from the same header:
+the recovery with the atmosphere and floor rules (`recover`) against the oracle's recovery of the
+step, and the CFL maximum (`cell_max_speed`) against the oracle's."""
 import ctypes
 import os
 import subprocess
@@ -40,6 +42,10 @@ def dev():
     ci, cd = ctypes.c_int, ctypes.c_double
     L.dev_rhs.argtypes = [ip, dp, ip, cd, ci, cd, cd, ci, ci, ci, dp, dp, dp]
     L.dev_rhs.restype = ci
+    L.dev_recover.argtypes = [ctypes.c_long, cd, ci, ci, cd, cd, cd, cd, ci, cd, dp, dp, dp, dp, ip]
+    L.dev_recover.restype = None
+    L.dev_max_speed.argtypes = [ip, dp, ip, cd, ci, cd, ci, dp, dp]
+    L.dev_max_speed.restype = cd
     return L
 
 
@@ -115,3 +121,71 @@ def test_cases_exercise_the_method():
     assert np.ptp(P.metric[0]) > 0.01
     P, _ = CASES["balsara1_x"]
     assert np.ptp(P.prim[0]) > 0.5
+
+
+def _bad_energy(cons):
+    cons[::7, 1] = -0.3 * cons[::7, 0]  # energy below the rest mass: no physical state
+
+
+@pytest.mark.parametrize("diag", [0, 1])
+@pytest.mark.parametrize("clean", [0, 1])
+@pytest.mark.parametrize("rule", ["plain", "atmosphere", "pressure_floor", "unphysical"])
+def test_recovery_with_atmosphere_and_floors_matches_oracle(dev, diag, clean, rule):
+    """Same failures, same resets, same primitive and rewritten conserved states."""
+    n, gamma = 400, 5.0 / 3.0
+    rho_floor, p_floor, atm_K, rho_atm, mutate = 1e-12, 1e-14, 0.0, 0.0, None
+    if rule == "atmosphere":
+        rho_floor, atm_K, rho_atm = 1e-7, 100.0, 1e-5
+    elif rule == "pressure_floor":
+        p_floor = 1e-4
+    elif rule == "unphysical":
+        mutate = _bad_energy
+    met = W.random_metric_points(n, seed=91)
+    if diag:
+        met[:, 1:4] = 0.0
+        met[:, [5, 6, 8]] = 0.0
+    met = np.ascontiguousarray(met)
+    prim = np.ascontiguousarray(W.random_prim_points(n, seed=92, met=met, wmax=5.0, sigma_max=10.0))
+    prim[:, 8] = np.random.Generator(np.random.PCG64(93)).uniform(-0.05, 0.05, n) if clean else 0.0
+    opts = O.make_opts(gamma, cleaning=bool(clean), rho_floor=rho_floor, p_floor=p_floor, atm_K=atm_K,
+                       rho_atm=rho_atm)
+    cons = O.prim2cons(opts, met, prim)
+    if mutate is not None:
+        mutate(cons)
+    rng = np.random.Generator(np.random.PCG64(94))
+    guess = np.ascontiguousarray(prim * (1.0 + 0.05 * rng.uniform(-1.0, 1.0, prim.shape)))
+    want_p, want_u, want_s = O.recover(opts, met, cons, guess)
+    p_atm = max(atm_K * rho_floor ** gamma if atm_K > 0 else p_floor, p_floor)
+    got_u = np.ascontiguousarray(cons.copy())
+    got_p = np.zeros((n, 9))
+    got_s = np.zeros(n, dtype=np.int32)
+    dp = ctypes.POINTER(ctypes.c_double)
+    dev.dev_recover(n, gamma, clean, diag, rho_floor, p_floor, p_atm, rho_atm, 200, 1e-14,
+                    met.ctypes.data_as(dp), got_u.ctypes.data_as(dp), guess.ctypes.data_as(dp),
+                    got_p.ctypes.data_as(dp), got_s.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    nf = 9 if clean else 8
+    assert np.array_equal(got_s, want_s)
+    if rule == "unphysical":
+        assert want_s.sum() > 0
+    if rule in ("atmosphere", "pressure_floor"):
+        assert np.any(np.abs(want_u - cons).max(axis=1) > 0)  # some cells were reset
+    for got, want in ((got_p, want_p), (got_u, want_u)):
+        scale = np.maximum(np.abs(want[:, :nf]).max(axis=1, keepdims=True), 1e-300)
+        assert (np.abs(got[:, :nf] - want[:, :nf]) / scale).max() < 1e-12  # measured <= 9.3e-14
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("clean", [0, 1])
+def test_cfl_maximum_matches_oracle(dev, case, clean):
+    P, diag = CASES[case]
+    n = (ctypes.c_int * 3)(*P.n)
+    dx = (ctypes.c_double * 3)(*P.dx)
+    bc = (ctypes.c_int * 3)(*P.bc)
+    met = np.ascontiguousarray(P.metric, dtype=np.float64)
+    prim = np.ascontiguousarray(P.prim, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    got = dev.dev_max_speed(n, dx, bc, P.gamma, clean, P.ch, diag, met.ctypes.data_as(dp),
+                            prim.ctypes.data_as(dp))
+    want = O.max_speed(O.make_grid(P.n, P.dx, P.bc), O.make_opts(P.gamma, cleaning=bool(clean), ch=P.ch),
+                       met, prim)
+    assert got == pytest.approx(want, rel=1e-14)
