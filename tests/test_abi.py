@@ -51,6 +51,14 @@ def test_workspace_bytes_and_argument_checks(lib):
     assert nb < (10 * msize + 4 * 9 * 192 ** 3 + 55 * msize + 4096) * 8
     bad = [
         (hzn.make_grid((1, 4, 4), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_UNSUPPORTED),
+        # degenerate grids: empty, negative, a single cell (no active axis)
+        (hzn.make_grid((0, 1, 1), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_ARG),
+        (hzn.make_grid((8, 0, 1), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_ARG),
+        (hzn.make_grid((-4, 1, 1), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_ARG),
+        (hzn.make_grid((1, 1, 1), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_UNSUPPORTED),
+        # sizes whose index arithmetic or workspace would overflow
+        (hzn.make_grid((2 ** 31 - 1, 1, 1), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_ARG),
+        (hzn.make_grid((2 ** 20, 2 ** 20, 2 ** 20), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_ARG),
         (hzn.make_grid((8, 1, 4), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_UNSUPPORTED),
         (hzn.make_grid((8, 8, 8), (1, 0, 1), (0, 0, 0)), o, hzn.HZ_ERR_ARG),
         (hzn.make_grid((8, 8, 8), (1, 1, 1), (0, 2, 0)), o, hzn.HZ_ERR_ARG),
