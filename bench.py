@@ -184,6 +184,40 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- GPU arm
+def fp64_roofline(cells: int, substep_s: float) -> dict:
+    """ALU roofline of the FP64 substep kernel: the method's algorithmic flops per launch over
+    the mean launch duration against the measured DFMA peak, with the kernel's executed FP64
+    flops and instructions beside it."""
+    ach = FP64_ALG_FLOPS_PER_ZU / 3.0 * cells / substep_s / 1e12
+    impl = FP64_FLOPS_PER_CELL_SUBSTEP * cells / substep_s / 1e12
+    inst = FP64_INST_PER_CELL_SUBSTEP * cells / substep_s
+    return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS,
+            "traffic": DRAM_BYTES_PER_CELL_SUBSTEP * cells if DRAM_BYTES_PER_CELL_SUBSTEP else None,
+            "kernel": "k_substep<32,4,3-D,cleaning,diag,FP64,MC>", "peak_source": "measured FP64 DFMA loop",
+            "algorithmic_flops_per_zu": FP64_ALG_FLOPS_PER_ZU,
+            "implemented_fp64_flops": {"per_cell_substep": FP64_FLOPS_PER_CELL_SUBSTEP, "achieved": impl,
+                                       "frac": impl / FP64_PEAK_TFLOPS},
+            "fp64_instructions": {"per_cell_substep": FP64_INST_PER_CELL_SUBSTEP, "achieved_per_s": inst,
+                                  "peak_per_s": FP64_INST_PEAK_PER_S, "frac": inst / FP64_INST_PEAK_PER_S}}
+
+
+def mixed_roofline(cells: int, substep_s: float) -> dict:
+    """ALU roofline of the mixed-precision substep kernel: the algorithmic flops of the phases
+    it keeps in FP64 against the DFMA peak, those of its FP32 phases against the FFMA peak."""
+    fl = ALG_FLOPS_PER_ZU_FP64_PHASES / 3.0 * cells / substep_s / 1e12
+    fl32 = (FP64_ALG_FLOPS_PER_ZU - ALG_FLOPS_PER_ZU_FP64_PHASES) / 3.0 * cells / substep_s / 1e12
+    impl = MIXED_FP64_FLOPS_PER_CELL_SUBSTEP * cells / substep_s / 1e12
+    return {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": fl / FP64_PEAK_TFLOPS,
+            "traffic": MIXED_DRAM_BYTES_PER_CELL_SUBSTEP * cells if MIXED_DRAM_BYTES_PER_CELL_SUBSTEP else None,
+            "kernel": "k_substep<32,4,3-D,cleaning,diag,mixed> (FP64 recovery and update)",
+            "algorithmic_flops_per_zu_fp64_phases": ALG_FLOPS_PER_ZU_FP64_PHASES,
+            "implemented_fp64_flops": {"per_cell_substep": MIXED_FP64_FLOPS_PER_CELL_SUBSTEP,
+                                       "achieved": impl, "frac": impl / FP64_PEAK_TFLOPS},
+            "fp32_phases": {"achieved": fl32, "peak": FP32_PEAK_TFLOPS, "frac": fl32 / FP32_PEAK_TFLOPS}}
+
+
 def run_gpu(args, rank, world, local):
     import torch
 
@@ -232,22 +266,7 @@ def run_gpu(args, rank, world, local):
 
     # roofline of the dominant kernel (the fused substep): three launches per step
     substep_s = statistics.mean(step_ms) * 1e-3 / 3.0
-    if FP64_ALG_FLOPS_PER_ZU:
-        ach = FP64_ALG_FLOPS_PER_ZU / 3.0 * cells / substep_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": DRAM_BYTES_PER_CELL_SUBSTEP * cells if DRAM_BYTES_PER_CELL_SUBSTEP else None,
-                "kernel": "k_substep<32,4,3-D,cleaning,diag,FP64,MC>", "peak_source": "measured FP64 DFMA loop",
-                "algorithmic_flops_per_zu": FP64_ALG_FLOPS_PER_ZU}
-        impl = FP64_FLOPS_PER_CELL_SUBSTEP * cells / substep_s / 1e12
-        roof["implemented_fp64_flops"] = {"per_cell_substep": FP64_FLOPS_PER_CELL_SUBSTEP, "achieved": impl,
-                                          "frac": impl / FP64_PEAK_TFLOPS}
-        inst = FP64_INST_PER_CELL_SUBSTEP * cells / substep_s
-        roof["fp64_instructions"] = {"per_cell_substep": FP64_INST_PER_CELL_SUBSTEP, "achieved_per_s": inst,
-                                     "peak_per_s": FP64_INST_PEAK_PER_S, "frac": inst / FP64_INST_PEAK_PER_S}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "kernel": "k_substep<32,4,3-D,cleaning>"}
+    roof = fp64_roofline(cells, substep_s)
     hbm_peak = json.load(open(MEASURED_PEAKS))["hbm_gbs"] if os.path.exists(MEASURED_PEAKS) else 6800.0
     hbm_ach = HBM_BYTES_PER_ZU / 3.0 * cells / substep_s / 1e9
     hbm = {"bytes_per_zu": HBM_BYTES_PER_ZU, "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
@@ -343,25 +362,13 @@ def run_mixed(args, dist, local, hbm_peak):
     value = units / seconds
     ach = HBM_BYTES_PER_ZU_MIXED * value / world_size(dist) / 1e9
     substep_s = sec / args.steps / 3.0
-    fl = ALG_FLOPS_PER_ZU_FP64_PHASES / 3.0 * P.ncell / substep_s / 1e12
-    fl32 = (FP64_ALG_FLOPS_PER_ZU - ALG_FLOPS_PER_ZU_FP64_PHASES) / 3.0 * P.ncell / substep_s / 1e12
-    impl = MIXED_FP64_FLOPS_PER_CELL_SUBSTEP * P.ncell / substep_s / 1e12
     del s
     torch.cuda.empty_cache()
     err = mixed_error(P) if args.mixed_error else None
     return {"value": value, "unit": UNIT, "workload": f"blob3d_{args.n_mixed}^3_mixed_cleaning",
             "error_vs_fp64_gpu_100_steps": err,
             "cells": P.ncell, "ms_per_step": seconds / args.steps * 1e3, "dtype": "f32/f64",
-            "roofline": {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": fl / FP64_PEAK_TFLOPS,
-                         "traffic": (MIXED_DRAM_BYTES_PER_CELL_SUBSTEP * P.ncell
-                                     if MIXED_DRAM_BYTES_PER_CELL_SUBSTEP else None),
-                         "kernel": "k_substep<32,4,3-D,cleaning,diag,mixed> (FP64 recovery and update)",
-                         "algorithmic_flops_per_zu_fp64_phases": ALG_FLOPS_PER_ZU_FP64_PHASES,
-                         "implemented_fp64_flops": {"per_cell_substep": MIXED_FP64_FLOPS_PER_CELL_SUBSTEP,
-                                                    "achieved": impl, "frac": impl / FP64_PEAK_TFLOPS},
-                         "fp32_phases": {"achieved": fl32, "peak": FP32_PEAK_TFLOPS,
-                                         "frac": fl32 / FP32_PEAK_TFLOPS}},
+            "roofline": mixed_roofline(P.ncell, substep_s),
             "hbm_roofline": {"bytes_per_zu": HBM_BYTES_PER_ZU_MIXED, "achieved": ach, "peak": hbm_peak,
                              "unit": "GB/s", "frac": ach / hbm_peak,
                              "roofline_zu_per_s": hbm_peak * 1e9 / HBM_BYTES_PER_ZU_MIXED},
