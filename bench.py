@@ -39,6 +39,9 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # (profiles/fp64_alu_peak.md): 2 DFMA per clock per SM x 152 SMs.
 FP64_PEAK_TFLOPS = 1.194
 FP32_PEAK_TFLOPS = 72.98  # FFMA loop of the same probe, 8 blocks per SM
+# Double-word (pair-of-FP32) multiply-add loop of the same probe: 1.98e12 per second, two flops
+# each -- the rate of the double-word path's face arithmetic.
+DW_PEAK_TFLOPS = 3.96
 # Algorithmic flops per zone update (one cell, one RK3 step) of the method on the blob
 # workload at 192^3 (MC, cleaning on, CFL 0.5), from the op-counting oracle
 # (oracle/opcount_blob3d.json, written by oracle/write_counts.py): the floating-point operations
@@ -216,6 +219,19 @@ def mixed_roofline(cells: int, substep_s: float) -> dict:
             "implemented_fp64_flops": {"per_cell_substep": MIXED_FP64_FLOPS_PER_CELL_SUBSTEP,
                                        "achieved": impl, "frac": impl / FP64_PEAK_TFLOPS},
             "fp32_phases": {"achieved": fl32, "peak": FP32_PEAK_TFLOPS, "frac": fl32 / FP32_PEAK_TFLOPS}}
+
+
+def dw_roofline(cells: int, substep_s: float) -> dict:
+    """ALU roofline of the double-word face path: the algorithmic flops of its face phases
+    (reconstruction to sources, in pair-of-FP32 arithmetic) against the measured double-word
+    multiply-add rate, those of its FP64 phases (update, recovery, CFL) against the DFMA peak."""
+    f64 = ALG_FLOPS_PER_ZU_FP64_PHASES / 3.0 * cells / substep_s / 1e12
+    fdw = (FP64_ALG_FLOPS_PER_ZU - ALG_FLOPS_PER_ZU_FP64_PHASES) / 3.0 * cells / substep_s / 1e12
+    return {"bound": "alu", "achieved": fdw, "peak": DW_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": fdw / DW_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_substep<32,4,3-D,cleaning,diag,FP64 state,double-word faces>",
+            "peak_source": "measured double-word multiply-add loop (2 flops each)",
+            "fp64_phases": {"achieved": f64, "peak": FP64_PEAK_TFLOPS, "frac": f64 / FP64_PEAK_TFLOPS}}
 
 
 def run_gpu(args, rank, world, local):
@@ -550,6 +566,7 @@ def run_dw(args, dist, local, base_zu_per_s: float, steps: int = 10, warmup: int
             "steps": steps, "ms_per_step": seconds / steps * 1e3,
             "relative_to_fp64": units / seconds / base_zu_per_s,
             "rel_l1_vs_fp64_gpu": rel, "c2p_failures": int(st.c2p_failures),
+            "roofline": dw_roofline(P.ncell, seconds / steps / 3.0),
             "dtype": "f64 state / f32x2 faces", "gpu_launches": 4 * steps}
 
 

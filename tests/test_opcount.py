@@ -137,3 +137,8 @@ def test_benchmark_roofline_objects():
     json.dumps(m)
     assert m["achieved"] + m["fp32_phases"]["achieved"] == pytest.approx(
         bench.FP64_ALG_FLOPS_PER_ZU / 3 * cells / (t / 8) / 1e12)
+    d = bench.dw_roofline(cells, t / 1.5)
+    json.dumps(d)
+    assert d["achieved"] + d["fp64_phases"]["achieved"] == pytest.approx(
+        bench.FP64_ALG_FLOPS_PER_ZU / 3 * cells / (t / 1.5) / 1e12)
+    assert d["frac"] == pytest.approx(d["achieved"] / bench.DW_PEAK_TFLOPS)
