@@ -488,3 +488,27 @@ def test_failed_recovery_resets_to_atmosphere():
     assert np.all(prim2[:, 0] == 1e-9) and np.all(prim2[:, 2:5] == 0.0)
     assert np.allclose(prim2[:, 5:8], U[:, 5:8] / (alp * sqrtg)[:, None], rtol=1e-14, atol=0)
     assert np.allclose(U2, O.prim2cons(opts, met, prim2), rtol=1e-14, atol=1e-300)
+
+
+def test_mc_reconstruction_special_cases():
+    """TVD MC (§3.2): exact on linear data; a flat slope in a cell at a local extremum; and
+    each branch of min(2|dm|, 2|dp|, |dm + dp| / 2) with its sign, on hand-computed cells.
+    The face between cells 4 and 5 takes left = q4 + s4 / 2 and right = q5 - s5 / 2."""
+    i = np.arange(14, dtype=float)
+    q = 0.3 - 1.7 * i
+    left, right = O.reconstruct_1d(O.RECON_MC, q)
+    faces = np.arange(3, 12)
+    exact = 0.3 - 1.7 * (faces - 0.5)
+    assert np.allclose(left[faces], exact, rtol=0, atol=1e-14)
+    assert np.allclose(right[faces], exact, rtol=0, atol=1e-14)
+    # (q3, q4, q5, q6) -> (left[5], right[5]), slopes worked out by hand:
+    cases = [
+        ((0.0, 1.0, 3.0, 3.0), (1.75, 3.0)),    # s4 = |dm+dp|/2 = 1.5; s5: dp = 0, flat
+        ((0.0, 1.0, 10.0, 12.0), (2.0, 8.0)),   # s4 = 2|dm| = 2; s5 = 2|dp| = 4
+        ((0.0, 9.0, 10.0, 9.0), (10.0, 10.0)),  # s4 = 2|dp| = 2; s5: extremum, flat
+        ((3.0, 1.0, 0.0, -4.0), (0.25, 1.0)),   # s4 = -1.5 (central); s5 = -2|dm| = -2
+    ]
+    for (a, b, c, d), (wl, wr) in cases:
+        q = np.array([a, a, a, a, b, c, d, d, d, d])
+        left, right = O.reconstruct_1d(O.RECON_MC, q)
+        assert (left[5], right[5]) == (wl, wr), (a, b, c, d)
