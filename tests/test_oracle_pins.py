@@ -512,3 +512,36 @@ def test_mc_reconstruction_special_cases():
         q = np.array([a, a, a, a, b, c, d, d, d, d])
         left, right = O.reconstruct_1d(O.RECON_MC, q)
         assert (left[5], right[5]) == (wl, wr), (a, b, c, d)
+
+
+def test_hlle_reduces_to_upwinding_when_all_waves_move_right():
+    """HLLE (§2.2) with s_L = min(0, lambda-) = 0: the face flux is the left state's flux, so
+    on a cold, fast flow to +x (every wave speed positive at every face) the right-hand side is
+    minus the difference of the fluxes of the left face states, reconstructed by MC."""
+    n, dx, gamma = 32, 1.0 / 32, 5.0 / 3.0
+    x = (np.arange(n) + 0.5) * dx
+    prim = np.zeros((9, 1, 1, n))
+    prim[0, 0, 0] = 1.0 + 0.2 * np.sin(2 * np.pi * x)
+    prim[1, 0, 0] = 1e-3 * (1.0 + 0.5 * np.cos(2 * np.pi * x))
+    prim[2, 0, 0] = 3.0                                  # u~^x: v^x = 0.95
+    prim[3, 0, 0] = 0.1 * np.sin(4 * np.pi * x)
+    prim[5, 0, 0] = 0.05
+    prim[6, 0, 0] = 0.02 * np.cos(2 * np.pi * x)
+    met = W.minkowski_metric((n, 1, 1))
+    grid = O.make_grid((n, 1, 1), (dx, 1.0, 1.0), (1, 1, 1))
+    opts = O.make_opts(gamma)
+    L = O.rhs(grid, opts, met, prim)
+    # left face states at faces i - 1/2, i = 0 .. n (periodic: pad three cells each side)
+    ext = np.concatenate([prim[:, 0, 0, -3:], prim[:, 0, 0], prim[:, 0, 0, :3]], axis=1)
+    faces = [O.reconstruct_1d(O.RECON_MC, ext[f]) for f in range(9)]
+    PL = np.stack([lr[0] for lr in faces], axis=1)[3:3 + n + 1]  # faces of cells 0 .. n
+    PR = np.stack([lr[1] for lr in faces], axis=1)[3:3 + n + 1]
+    mrow = np.tile([1.0, 0, 0, 0, 1.0, 0, 0, 1.0, 0, 1.0], (n + 1, 1))
+    for P in (PL, PR):                                    # the premise: supersonic everywhere
+        assert O.speeds(opts, 0, mrow, P).min() > 0.0
+    F = O.flux(opts, 0, mrow, PL)
+    want = -(F[1:] - F[:-1]) / dx                         # (n, 9)
+    got = L[:, 0, 0, :].T
+    scale = np.abs(want).max(axis=0)
+    for f in range(8):
+        assert np.abs(got[:, f] - want[:, f]).max() <= 1e-12 * max(scale[f], 1e-300), f
