@@ -678,10 +678,7 @@ def oracle_sample(P, m: int):
     return P.subbox((lo,) * 3, (lo + m,) * 3, name=f"{P.name}_sample{m}")
 
 
-def run_cpu_baseline(P, seconds_target=15.0, m=48):
-    import oracle as O
-
-    Q = oracle_sample(P, m)
+def _time_oracle_steps(O, Q, seconds_target):
     grid = O.make_grid(Q.n, Q.dx, Q.bc)
     opts = O.make_opts(Q.gamma, cleaning=Q.cleaning, ch=Q.ch, kappa=Q.kappa, rho_floor=Q.rho_floor,
                        p_floor=Q.p_floor, atm_K=Q.atm_K, rho_atm=Q.rho_atm)
@@ -695,10 +692,30 @@ def run_cpu_baseline(P, seconds_target=15.0, m=48):
         steps += 1
         if time.perf_counter() - t0 >= seconds_target or steps >= 1000:
             break
-    sec = time.perf_counter() - t0
-    return {"value": Q.ncell * steps / sec, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{steps} RK3 step(s) of the central {m}^3 sub-box of the {P.n[0]}^3 blob, "
-                      f"{sec:.1f} s"}
+    return steps, time.perf_counter() - t0
+
+
+def run_cpu_baseline(P, seconds_target=15.0, m=48, m_single=24, seconds_single=6.0):
+    """The oracle on the host cores (OpenMP over all of them) on the central m^3 sub-box of the
+    benchmark blob, and on one core on a smaller sub-box."""
+    import oracle as O
+
+    Q = oracle_sample(P, m)
+    cores = O.num_threads()
+    steps, sec = _time_oracle_steps(O, Q, seconds_target)
+    out = {"value": Q.ncell * steps / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{steps} RK3 step(s) of the central {m}^3 sub-box of the {P.n[0]}^3 blob, "
+                     f"{sec:.1f} s"}
+    Q1 = oracle_sample(P, m_single)
+    O.set_num_threads(1)
+    try:
+        steps1, sec1 = _time_oracle_steps(O, Q1, seconds_single)
+    finally:
+        O.set_num_threads(cores)
+    out["single_thread"] = {"value": Q1.ncell * steps1 / sec1, "unit": UNIT, "cores": 1,
+                            "sample": f"{steps1} RK3 step(s) of the central {m_single}^3 sub-box, "
+                                      f"{sec1:.1f} s"}
+    return out
 
 
 def run_reference(args, rank, world):

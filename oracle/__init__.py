@@ -95,6 +95,8 @@ def lib():
             L.hzo_evolve_cs.restype = ctypes.c_long
             L.hzo_reconstruct_1d.argtypes = [ctypes.c_int, ctypes.c_long, dp, dp, dp]
             L.hzo_num_threads.restype = ctypes.c_int
+            L.hzo_set_num_threads.argtypes = [ctypes.c_int]
+            L.hzo_set_num_threads.restype = None
             _lib = L
     return _lib
 
@@ -129,6 +131,11 @@ def make_grid(n, dx, bc) -> Grid:
 
 def num_threads() -> int:
     return int(lib().hzo_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the grid operations from now on."""
+    lib().hzo_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- pointwise helpers

@@ -1003,4 +1003,13 @@ int hzo_num_threads(void) {
 #endif
 }
 
+// Threads of the grid operations from now on (n >= 1); no effect without OpenMP.
+void hzo_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 }  // extern "C"
