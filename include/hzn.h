@@ -102,7 +102,7 @@ typedef struct {
 typedef struct {
   long long c2p_failures; /* cells reset to atmosphere since the last hz_set_primitives     */
   int c2p_max_iters;      /* largest Newton iteration count seen since then                 */
-  double max_speed;       /* max over cells and active axes of max|lambda|/dx, newest state */
+  double max_speed;       /* CFL rate of the newest state (see hz_max_speed)                */
   double t;               /* simulated time since the last hz_set_primitives               */
   double dt;              /* step size of the last step                                     */
   long long steps;        /* full RK3 steps since the last hz_set_primitives               */
@@ -145,8 +145,10 @@ int hz_step(hz_ctx* ctx, double dt);
  * synchronisation, so a sequence of calls can be captured in a CUDA graph. */
 int hz_step_cfl(hz_ctx* ctx, double cfl, double t_end);
 
-/* Maximum over cells and active axes of max(|lambda+|, |lambda-|)/dx of the current state
- * (with the cleaning speed when cleaning is on).  Synchronises the stream. */
+/* CFL rate of the current state: the maximum over cells of the sum over active axes of
+ * max(|lambda+|, |lambda-|)/dx (each axis's bound widened to the cleaning speed when cleaning is
+ * on), so that dt = cfl / rate; the RK3 update treats all axes at once (§3.2), so their Courant
+ * numbers add.  In 1-D, the per-axis maximum.  Synchronises the stream. */
 int hz_max_speed(hz_ctx* ctx, double* h_out);
 
 /* Statistics of the run so far.  Synchronises the stream.  Returns HZ_WARN_C2P when

@@ -28,7 +28,10 @@
 //     (B^d, Psi) uses HLLE bounds -beta^d -+ c_h alpha sqrt(gamma^dd);
 //   * floors: a cell with D/sqrt(gamma) < rho_atm, a failed recovery, or a recovered
 //     rho < rho_floor is set to atmosphere (rho_floor, p_atm, zero velocity, same B and psi);
-//     p < p_floor is raised to p_floor; every reset recomputes the conserved vector.
+//     p < p_floor is raised to p_floor; every reset recomputes the conserved vector;
+//   * the time step is dt = CFL / max over cells of sum_d max|lambda_d| / dx_d, the Courant
+//     condition of an update that treats all axes at once (the same as the per-axis form in
+//     1-D).
 //
 // Every function is written for a scalar type R: double, or std::complex<double> for
 // complex-step differentiation (d J / d q = Im J(q + i h) / h, exact to round-off for the
@@ -904,7 +907,11 @@ void hzo_rhs(const hzo_grid* g, const hzo_opts* o, const double* met, const doub
   std::memcpy(L, Lv.data(), sizeof(double) * Lv.size());
 }
 
-// max over cells and active axes of max(|l+|, |l-|) / dx_d (with the cleaning speed when on).
+// The CFL rate: max over cells of the sum over active axes of max(|l+|, |l-|) / dx_d (with the
+// cleaning speed when on), so that dt = CFL / rate.  The RK3 stages update all axes at once
+// (§3.2), so a grid-scale mode along a diagonal sees the sum of the axes' Courant numbers; with
+// the per-axis maximum instead, CFL 0.5 in 3-D puts that mode at -3 on the real axis, outside
+// RK3's stability interval [-2.51, 0].  In 1-D both definitions coincide.
 double hzo_max_speed(const hzo_grid* g, const hzo_opts* o, const double* met, const double* prim) {
   Mesh M(*g);
   const long nc = M.ncell;
@@ -919,6 +926,7 @@ double hzo_max_speed(const hzo_grid* g, const hzo_opts* o, const double* met, co
     for (int f = 0; f < NPRIM; ++f) P[f] = prim[(size_t)f * nc + c];
     Geom<double> G = make_geom(m);
     State<double> S = make_state(G, P, o->gamma);
+    double rate = 0.0;
     for (int d = 0; d < 3; ++d) {
       if (!M.act[d]) continue;
       double lm, lp;
@@ -929,9 +937,9 @@ double hzo_max_speed(const hzo_grid* g, const hzo_opts* o, const double* met, co
         clean_speeds(G, d, o->ch, &cm, &cp);
         v = std::max(v, std::max(std::fabs(cm), std::fabs(cp)));
       }
-      v = v / g->dx[d];
-      if (v > vmax) vmax = v;
+      rate += v / g->dx[d];
     }
+    if (rate > vmax) vmax = rate;
   }
   return vmax;
 }
