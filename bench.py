@@ -48,11 +48,11 @@ DW_PEAK_TFLOPS = 3.96
 # (+, -, *, /, sqrt) that each face's and each cell's results and decisions depend on, each
 # counted once, operations on structural zeros of the diagonal spacetime and the static
 # geometry excluded.  The roofline's achieved rate is this count over the measured time.
-FP64_ALG_FLOPS_PER_ZU = 3899.1264114379883
+FP64_ALG_FLOPS_PER_ZU = 3898.8812772962783
 # The part of it in the phases the mixed path keeps in FP64 (RK update, recovery, CFL maximum);
 # the rest (reconstruction, face states, fluxes, speeds, HLLE, divergence, sources) runs in FP32
 # there.
-ALG_FLOPS_PER_ZU_FP64_PHASES = 308.9395263106735
+ALG_FLOPS_PER_ZU_FP64_PHASES = 308.66399468315973
 # FP64 operations per cell per substep executed by the fused substep kernel (3-D, cleaning
 # on, diagonal metric with its geometry tables), from ncu instruction counters on the 128^3
 # blob (profiles/k_substep_blob3d.md): DFMA counted as 2 flops, DADD/DMUL as 1.  Reported
