@@ -48,6 +48,26 @@ def test_balsara1_to_end_time():
     assert np.all(gp[5] == 0.5)  # B^x stays exactly constant in 1-D
 
 
+@pytest.mark.parametrize("case", ["blob_diag", "general_2d", "general_3d_cleaning"])
+def test_device_cfl_rate_multi_d_matches_oracle(case):
+    """The CFL rate in 2-D and 3-D (the sum over active axes of max|lambda|/dx, with the
+    cleaning speed when on) on the device equals the oracle's, and the device's CFL step uses it."""
+    if case == "blob_diag":
+        P = W.blob3d(24)
+    else:
+        P = W.smooth_periodic((37, 11, 7) if case.endswith("3d_cleaning") else (70, 9, 1), seed=5,
+                              amp=0.2, magnetised=True)
+        P = W.with_periodic_metric(P, general_metric)
+        if case.endswith("cleaning"):
+            P.cleaning, P.ch, P.kappa = True, 0.9, 0.7
+    s = gpu_solver(P)
+    grid, opts = oracle_setup(P)
+    want = O.max_speed(grid, opts, P.metric, P.prim)
+    assert s.max_speed() == pytest.approx(want, rel=1e-13)
+    s.step_cfl(0.5, 1e30)
+    assert s.stats().dt == pytest.approx(0.5 / want, rel=1e-13)
+
+
 def test_device_cfl_matches_oracle_dt():
     P = W.balsara1(400)
     s = gpu_solver(P)
