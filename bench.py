@@ -326,7 +326,7 @@ def run_gpu(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"blob3d_{args.n}^3_fp64_cleaning", "cells": cells,
                        "domain": "[-20,20]^3", "metric": "capped isotropic Schwarzschild M=1.4",
-                       "cfl": 0.5, "parallelism": "replicas" if world > 1 else "single",
+                       "cfl": 0.5, "courant": "sum over axes", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "state larger than L2 (no flush)"},
             "roofline": roof,
             "hbm_roofline": hbm,
