@@ -25,7 +25,9 @@
 //   * divergence cleaning (§3.2): generalised-Lagrange-multiplier field psi with conserved
 //     Psi = sqrt(gamma) psi, extra flux sqrt(-g) gamma^{dj} psi on B^j, flux
 //     sqrt(gamma)(c_h^2 alpha^2 B^d - beta^d psi) on Psi, source -kappa alpha Psi; the pair
-//     (B^d, Psi) uses HLLE bounds -beta^d -+ c_h alpha sqrt(gamma^dd);
+//     (B^d, Psi) uses HLLE bounds at its own characteristic speeds,
+//     -beta^d / 2 -+ sqrt((beta^d / 2)^2 + c_h^2 alpha^2 gamma^dd) (-+ c_h alpha sqrt(gamma^dd)
+//     without shift);
 //   * floors: a cell with D/sqrt(gamma) < rho_atm, a failed recovery, or a recovered
 //     rho < rho_floor is set to atmosphere (rho_floor, p_atm, zero velocity, same B and psi);
 //     p < p_floor is raised to p_floor; every reset recomputes the conserved vector;
@@ -271,12 +273,18 @@ static void speeds(const Geom<R>& G, const State<R>& S, int d, double gamma, R* 
   *lm = (-B - sq) / (2.0 * A);
 }
 
-// Coordinate speeds of the cleaning pair (B^d, Psi): -beta^d -+ c_h alpha sqrt(gamma^dd).
+// Characteristic speeds of the cleaning pair (B^d, Psi) along d.  In the conserved variables
+// (sqrt(-g) B^d, Psi) its fluxes are alpha gamma^dd Psi and c_h^2 alpha sqrt(-g) B^d - beta^d Psi
+// (the induction flux of B^d along d vanishes), so the speeds are the roots of
+// l^2 + beta^d l - c_h^2 alpha^2 gamma^dd = 0:  l = -beta^d / 2 -+ sqrt((beta^d / 2)^2 + a^2),
+// a = c_h alpha sqrt(gamma^dd); with zero shift, -+a.
 template <class R>
 static void clean_speeds(const Geom<R>& G, int d, double ch, R* lm, R* lp) {
   R a = ch * G.alp * std::sqrt(G.ginv[d][d]);
-  *lm = -G.beta[d] - a;
-  *lp = -G.beta[d] + a;
+  R hb = 0.5 * G.beta[d];
+  R r = std::sqrt(hb * hb + a * a);
+  *lm = -hb - r;
+  *lp = -hb + r;
 }
 
 // MC-limited slope (TVD reconstruction with the monotonized-central limiter, §3.2).

@@ -404,7 +404,9 @@ __device__ __forceinline__ void speed_quadratic(const Geom<R>& G, const State<R>
   sq = disc > R(0) ? disc * rsqrt(disc) : R(0);
 }
 
-// Coordinate speeds of the cleaning pair along D: -beta^D -+ c_h alpha sqrt(gamma^DD).
+// Characteristic speeds of the cleaning pair (B^D, Psi) along D:
+// -beta^D / 2 -+ sqrt((beta^D / 2)^2 + c_h^2 alpha^2 gamma^DD), i.e. -+ c_h alpha sqrt(gamma^DD)
+// with zero shift.
 template <int D, bool DIAG, typename R>
 __device__ __forceinline__ void clean_speeds(const Geom<R>& G, R ch, R& lm, R& lp) {
   const R a = ch * G.alp * sqrt(sel<D>(G.ixx, G.iyy, G.izz));
@@ -412,9 +414,12 @@ __device__ __forceinline__ void clean_speeds(const Geom<R>& G, R ch, R& lm, R& l
     lm = -a;
     lp = a;
   } else {
-    const R bd = sel<D>(G.bx, G.by, G.bz);
-    lm = -bd - a;
-    lp = -bd + a;
+    // roots of l^2 + beta^D l - a^2 = 0: the pair's fluxes are alpha gamma^DD Psi and
+    // c_h^2 alpha sqrt(-g) B^D - beta^D Psi
+    const R hb = R(0.5) * sel<D>(G.bx, G.by, G.bz);
+    const R r = sqrt(hb * hb + a * a);
+    lm = -hb - r;
+    lp = -hb + r;
   }
 }
 

@@ -602,3 +602,49 @@ def test_magnetised_moving_box_with_grid_noise_stays_bounded():
     assert t == pytest.approx(3.0) and fails == 0 and steps > 100
     assert np.abs(p[0] - 1.0).max() < 5 * np.abs(noise[0]).max()
     assert np.abs(p[1] - 1.0).max() < 5 * np.abs(noise[1]).max()
+
+
+def _shifted_flat_metric(n, beta):
+    met = np.zeros((10, 1, 1, n + 2))
+    met[0], met[1] = 1.0, beta
+    met[4], met[7], met[9] = 1.0, 1.0, 1.0
+    return met
+
+
+def test_cleaning_speeds_with_shift_closed_form():
+    """Flat spacetime with a uniform shift beta^x, gas at rest for the normal observers and
+    nearly cold, so the cleaning pair bounds the rate: its speeds are the roots of
+    l^2 + beta l - c_h^2 = 0, and the rate is max|l| / dx = (|beta| / 2 + sqrt(beta^2 / 4 + c_h^2)) / dx."""
+    n, dx, ch = 16, 0.05, 0.5
+    prim = np.zeros((9, 1, 1, n))
+    prim[0], prim[1] = 1.0, 1e-8
+    for beta in (0.3, -0.45):
+        grid = O.make_grid((n, 1, 1), (dx, 1.0, 1.0), (1, 1, 1))
+        rate = O.max_speed(grid, O.make_opts(5.0 / 3.0, cleaning=True, ch=ch), _shifted_flat_metric(n, beta),
+                           prim)
+        want = (abs(beta) / 2 + math.sqrt(beta * beta / 4 + ch * ch)) / dx
+        assert rate == pytest.approx(want, rel=1e-14)
+
+
+def test_cleaning_pulses_travel_at_the_pairs_speeds_with_shift():
+    """A psi pulse in flat spacetime with shift 0.3 splits into the pair's two characteristic
+    waves, at -beta/2 -+ sqrt(beta^2/4 + c_h^2) = 0.372 and -0.672 (not -beta -+ c_h)."""
+    n, L, ch, beta, T = 800, 4.0, 0.5, 0.3, 1.0
+    dx = L / n
+    x = (np.arange(n) + 0.5) * dx
+    prim = np.zeros((9, 1, 1, n))
+    prim[0], prim[1] = 1.0, 1.0
+    prim[8, 0, 0] = 1e-3 * np.exp(-((x - 2.0) / 0.05) ** 2)
+    met = _shifted_flat_metric(n, beta)
+    grid = O.make_grid((n, 1, 1), (dx, 1.0, 1.0), (1, 1, 1))
+    opts = O.make_opts(5.0 / 3.0, cleaning=True, ch=ch)
+    cons = O.grid_prim2cons(grid, opts, met, prim)
+    p, _, _, t, fails = O.evolve(grid, opts, met, prim, cons, T, 0.4)
+    assert fails == 0
+    psi = np.abs(p[8, 0, 0])
+    r = math.sqrt(beta * beta / 4 + ch * ch)
+    right, left = 2.0 + (-beta / 2 + r) * T, 2.0 + (-beta / 2 - r) * T
+    for want, lo, hi in ((right, 2.0, 3.0), (left, 1.0, 2.0)):
+        sel = (x > lo) & (x < hi)
+        got = x[sel][np.argmax(psi[sel])]
+        assert abs(got - want) < 4 * dx, (want, got)
