@@ -298,9 +298,11 @@ class Solver:
         hz_step(self.ctx, dt)
 
     def step_cfl(self, cfl: float, t_end: float):
+        """One RK3 step of dt = cfl / max_speed(), taken on the device, clipped at t_end."""
         hz_step_cfl(self.ctx, cfl, t_end)
 
     def max_speed(self) -> float:
+        """CFL rate of the current state: max over cells of sum_d max|lambda_d| / dx_d."""
         return hz_max_speed(self.ctx)
 
     def stats(self) -> hz_stats:
