@@ -648,3 +648,33 @@ def test_cleaning_pulses_travel_at_the_pairs_speeds_with_shift():
         sel = (x > lo) & (x < hi)
         got = x[sel][np.argmax(psi[sel])]
         assert abs(got - want) < 4 * dx, (want, got)
+
+
+def test_cleaning_damps_a_3d_divergence_error():
+    """3-D periodic box with a divergence error along the diagonal (B^x = 0.01 sin 2 pi (x+y+z))
+    beside a divergence-free field: with cleaning (c_h = 0.5, kappa = 5) the centred norm of
+    d_i(sqrt(-g) B^i) falls below 5 % of its start by t = 3; without cleaning only numerical
+    diffusion acts and it stays above half.  No recovery failure either way."""
+    n, dx = 16, 1.0 / 16
+    xs = (np.arange(n) + 0.5) * dx
+    Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+    prim = np.zeros((9, n, n, n))
+    prim[0], prim[1] = 1.0, 1.0
+    prim[5] = 0.01 * np.sin(2 * math.pi * (X + Y + Z))
+    prim[6] = 0.05 * np.sin(2 * math.pi * X)
+    met = W.minkowski_metric((n, n, n))
+    grid = O.make_grid((n, n, n), (dx, dx, dx), (1, 1, 1))
+
+    def norm(cons):
+        d = sum((np.roll(cons[5 + k], -1, axis=2 - k) - np.roll(cons[5 + k], 1, axis=2 - k)) / (2 * dx)
+                for k in range(3))
+        return float(np.sqrt((d ** 2).mean()))
+
+    ratios = {}
+    for cleaning, kappa in ((False, 0.0), (True, 5.0)):
+        opts = O.make_opts(5.0 / 3.0, cleaning=cleaning, ch=0.5 if cleaning else 0.0, kappa=kappa)
+        cons = O.grid_prim2cons(grid, opts, met, prim)
+        _, end, _, t, fails = O.evolve(grid, opts, met, prim, cons, 3.0, 0.5)
+        assert fails == 0 and t == pytest.approx(3.0)
+        ratios[cleaning] = norm(end) / norm(cons)
+    assert ratios[True] < 0.05 and ratios[False] > 0.5, ratios
