@@ -248,11 +248,13 @@ extern "C" int dev_rhs(const int* n, const double* dx, const int* bc, double gam
 
 // Recovery of n pointwise states with the kernels' atmosphere and floor rules (recover in
 // hzn_kernels.cuh): met n x 10, cons n x 9 (rewritten where a cell is reset), guess and prim
-// n x 9; status[i] = 1 where the root solve failed.  p_atm: the atmosphere pressure.
+// n x 9; status[i] = 1 where the root solve failed.  p_atm: the atmosphere pressure; one_d: the
+// one-dimensional Newton scheme (in z, v^2 eliminated) instead of the two-dimensional one.
 extern "C" void dev_recover(long n, double gamma, int clean, int diag, double rho_floor, double p_floor,
-                            double p_atm, double rho_atm, int maxit, double tol, const double* met,
+                            double p_atm, double rho_atm, int maxit, double tol, int one_d, const double* met,
                             double* cons, const double* guess, double* prim, int* status) {
   KParams kp = KParams{};
+  kp.c2p_1d = one_d;
   kp.gamma = gamma;
   kp.gfac = gamma / (gamma - 1.0);
   kp.rho_floor = rho_floor;

@@ -42,7 +42,7 @@ def dev():
     ci, cd = ctypes.c_int, ctypes.c_double
     L.dev_rhs.argtypes = [ip, dp, ip, cd, ci, cd, cd, ci, ci, ci, dp, dp, dp]
     L.dev_rhs.restype = ci
-    L.dev_recover.argtypes = [ctypes.c_long, cd, ci, ci, cd, cd, cd, cd, ci, cd, dp, dp, dp, dp, ip]
+    L.dev_recover.argtypes = [ctypes.c_long, cd, ci, ci, cd, cd, cd, cd, ci, cd, ci, dp, dp, dp, dp, ip]
     L.dev_recover.restype = None
     L.dev_max_speed.argtypes = [ip, dp, ip, cd, ci, cd, ci, dp, dp]
     L.dev_max_speed.restype = cd
@@ -130,8 +130,10 @@ def _bad_energy(cons):
 @pytest.mark.parametrize("diag", [0, 1])
 @pytest.mark.parametrize("clean", [0, 1])
 @pytest.mark.parametrize("rule", ["plain", "atmosphere", "pressure_floor", "unphysical"])
-def test_recovery_with_atmosphere_and_floors_matches_oracle(dev, diag, clean, rule):
-    """Same failures, same resets, same primitive and rewritten conserved states."""
+@pytest.mark.parametrize("one_d", [0, 1], ids=["newton2d", "newton1d"])
+def test_recovery_with_atmosphere_and_floors_matches_oracle(dev, diag, clean, rule, one_d):
+    """Same failures, same resets, same primitive and rewritten conserved states, with either
+    of the kernels' Newton schemes (§3.2 names a one- and a two-dimensional recovery)."""
     n, gamma = 400, 5.0 / 3.0
     rho_floor, p_floor, atm_K, rho_atm, mutate = 1e-12, 1e-14, 0.0, 0.0, None
     if rule == "atmosphere":
@@ -160,7 +162,7 @@ def test_recovery_with_atmosphere_and_floors_matches_oracle(dev, diag, clean, ru
     got_p = np.zeros((n, 9))
     got_s = np.zeros(n, dtype=np.int32)
     dp = ctypes.POINTER(ctypes.c_double)
-    dev.dev_recover(n, gamma, clean, diag, rho_floor, p_floor, p_atm, rho_atm, 200, 1e-14,
+    dev.dev_recover(n, gamma, clean, diag, rho_floor, p_floor, p_atm, rho_atm, 200, 1e-14, one_d,
                     met.ctypes.data_as(dp), got_u.ctypes.data_as(dp), guess.ctypes.data_as(dp),
                     got_p.ctypes.data_as(dp), got_s.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     nf = 9 if clean else 8
