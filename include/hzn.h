@@ -130,7 +130,7 @@ int hz_set_metric(hz_ctx* ctx, const double* d_metric);
 
 /* Copy the primitive state (9 x N doubles) into the workspace and compute the conserved
  * state w(u) per cell (§2.2: algebraic).  Resets time, step count and statistics, and
- * computes the maximum characteristic speed of the new state.  Requires hz_set_metric. */
+ * computes the CFL rate of the new state (see hz_max_speed).  Requires hz_set_metric. */
 int hz_set_primitives(hz_ctx* ctx, const double* d_prim);
 
 /* Copy out the current primitive / conserved state (9 x N doubles each). */
