@@ -747,7 +747,9 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": f"blob3d_{args.n}^3_fp64_cleaning", "cells": P.ncell,
-                       "sample_cells": Q.ncell, "parallelism": "host cores"},
+                       "domain": "[-20,20]^3", "metric": "capped isotropic Schwarzschild M=1.4",
+                       "cfl": 0.5, "courant": "sum over axes", "sample_cells": Q.ncell,
+                       "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
