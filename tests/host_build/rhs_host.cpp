@@ -6,7 +6,7 @@
 // uses.  Arrays in the oracle's layouts: met (10, nz+2gz, ny+2gy, nx+2gx), prim and out
 // (9, nz, ny, nx); inside, odd pitches and field strides with NaN padding, so that a read outside
 // the stencil or a wrong stride shows in the result.  Also the recovery with the atmosphere and
-// floor rules (recover) and the CFL maximum (cell_max_speed) of the same header.
+// floor rules (recover) and the CFL rate (cell_max_speed) of the same header.
 #include <cmath>
 #include <limits>
 #include <vector>
@@ -314,7 +314,7 @@ double max_speed_t(const Host& h) {
 
 }  // namespace
 
-// The CFL maximum over the grid, max over cells and active axes of max |lambda| / dx (with the
+// The CFL rate of the grid, max over cells of the sum over active axes of max |lambda| / dx (with the
 // cleaning speed when on), from the kernels' cell_max_speed; layouts as dev_rhs.
 extern "C" double dev_max_speed(const int* n, const double* dx, const int* bc, double gamma, int clean,
                                 double ch, int diag, const double* met, const double* prim) {

@@ -8,7 +8,8 @@ diagonal-metric star, smooth periodic data in a general metric (shift, non-diago
 CPU only: the same device templates, no GPU.  The harness pads the arrays with NaN and uses odd
 pitches, so a read outside the stencil or a wrong stride fails here.  Also from the same header:
 the recovery with the atmosphere and floor rules (`recover`) against the oracle's recovery of the
-step, and the CFL maximum (`cell_max_speed`) against the oracle's."""
+step, and the CFL rate (`cell_max_speed`: the largest per-cell sum over axes of |lambda| / dx)
+against the oracle's."""
 import ctypes
 import os
 import subprocess
