@@ -83,6 +83,7 @@ def lib():
             L.hzo_tensors.argtypes = [ctypes.c_long, op, dp, dp, dp, dp, dp]
             L.hzo_grid_prim2cons.argtypes = [gp, op, dp, dp, dp]
             L.hzo_rhs.argtypes = [gp, op, dp, dp, dp]
+            L.hzo_rhs_source.argtypes = [gp, op, dp, dp, dp]
             L.hzo_max_speed.argtypes = [gp, op, dp, dp]
             L.hzo_max_speed.restype = ctypes.c_double
             L.hzo_step.argtypes = [gp, op, dp, dp, dp, ctypes.c_double]
@@ -231,6 +232,14 @@ def rhs(grid: Grid, opts: Opts, met, prim) -> np.ndarray:
     met, prim = _f64(met), _f64(prim)
     out = np.empty_like(prim)
     lib().hzo_rhs(ctypes.byref(grid), ctypes.byref(opts), _dp(met), _dp(prim), _dp(out))
+    return out
+
+
+def rhs_source(grid: Grid, opts: Opts, met, prim) -> np.ndarray:
+    """The metric source and cleaning damping of ``rhs`` alone (no flux difference)."""
+    met, prim = _f64(met), _f64(prim)
+    out = np.empty_like(prim)
+    lib().hzo_rhs_source(ctypes.byref(grid), ctypes.byref(opts), _dp(met), _dp(prim), _dp(out))
     return out
 
 

@@ -621,6 +621,49 @@ static void fill_ghosts(const Mesh& M, const R* prim, std::vector<R>& Pp) {
       }
 }
 
+// Metric source S_mu = sqrt(-g) T^k_l Gamma^l_{mu k} = 1/2 sqrt(-g) T^{kl} d_mu g_{kl} of the
+// momentum equations (§2.1 Eq. 2), with d_i g_{kl} the centred difference (g(i+1) - g(i-1)) /
+// (2 dx_i) of the centre 4-metric; static metric: S_t = 0; mass and induction have no source.
+// Cleaning damping -kappa alpha Psi.  Added to L[f * ncell + cell].
+template <class R>
+static void add_sources(const Mesh& M, const hzo_opts& o, const double* met, const R* prim,
+                        std::vector<R>& L) {
+  const int* n = M.g.n;
+  const long nc = M.ncell;
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < nc; ++c) {
+    int i = (int)(c % n[0]);
+    int j = (int)((c / n[0]) % n[1]);
+    int k = (int)(c / ((long)n[0] * n[1]));
+    R m0[NMET];
+    load_metric(M, met, M.mcell(i, j, k), m0);
+    Geom<R> G = make_geom(m0);
+    R P[NPRIM];
+    for (int f = 0; f < NPRIM; ++f) P[f] = prim[(size_t)f * nc + c];
+    State<R> S = make_state(G, P, o.gamma);
+    for (int d = 0; d < 3; ++d) {
+      if (!M.act[d]) continue;
+      int e[3] = {0, 0, 0};
+      e[d] = 1;
+      R mp[NMET], mm[NMET];
+      load_metric(M, met, M.mcell(i + e[0], j + e[1], k + e[2]), mp);
+      load_metric(M, met, M.mcell(i - e[0], j - e[1], k - e[2]), mm);
+      Geom<R> Gp = make_geom(mp), Gm = make_geom(mm);
+      R src = 0.0;
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          R dg = (Gp.g4[a][b] - Gm.g4[a][b]) / (2.0 * M.g.dx[d]);
+          src += Tup(G, S, a, b) * dg;
+        }
+      L[(size_t)(CTX + d) * nc + c] += 0.5 * G.sqrtmg * src;
+    }
+    if (o.cleaning) {
+      R Psi = G.sqrtgam * S.psi;
+      L[(size_t)CPSI * nc + c] += -o.kappa * G.alp * Psi;
+    }
+  }
+}
+
 // Spatial operator L(U) = - sum_d (F_{d,i+1/2} - F_{d,i-1/2}) / dx_d + S (§2.2), from the
 // primitive state.  The result is stored in L[f * ncell + cell].
 template <class R>
@@ -695,40 +738,7 @@ static void rhs(const Mesh& M, const hzo_opts& o, const double* met, const R* pr
     }
   }
 
-  // Metric source S_mu = sqrt(-g) T^k_l Gamma^l_{mu k} = 1/2 sqrt(-g) T^{kl} d_mu g_{kl};
-  // static metric: S_t = 0.  Cleaning damping -kappa alpha Psi.
-#pragma omp parallel for schedule(static)
-  for (long c = 0; c < nc; ++c) {
-    int i = (int)(c % n[0]);
-    int j = (int)((c / n[0]) % n[1]);
-    int k = (int)(c / ((long)n[0] * n[1]));
-    R m0[NMET];
-    load_metric(M, met, M.mcell(i, j, k), m0);
-    Geom<R> G = make_geom(m0);
-    R P[NPRIM];
-    for (int f = 0; f < NPRIM; ++f) P[f] = prim[(size_t)f * nc + c];
-    State<R> S = make_state(G, P, o.gamma);
-    for (int d = 0; d < 3; ++d) {
-      if (!M.act[d]) continue;
-      int e[3] = {0, 0, 0};
-      e[d] = 1;
-      R mp[NMET], mm[NMET];
-      load_metric(M, met, M.mcell(i + e[0], j + e[1], k + e[2]), mp);
-      load_metric(M, met, M.mcell(i - e[0], j - e[1], k - e[2]), mm);
-      Geom<R> Gp = make_geom(mp), Gm = make_geom(mm);
-      R src = 0.0;
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) {
-          R dg = (Gp.g4[a][b] - Gm.g4[a][b]) / (2.0 * M.g.dx[d]);
-          src += Tup(G, S, a, b) * dg;
-        }
-      L[(size_t)(CTX + d) * nc + c] += 0.5 * G.sqrtmg * src;
-    }
-    if (o.cleaning) {
-      R Psi = G.sqrtgam * S.psi;
-      L[(size_t)CPSI * nc + c] += -o.kappa * G.alp * Psi;
-    }
-  }
+  add_sources(M, o, met, prim, L);
 }
 
 // Conserved state of the grid from its primitive state.
@@ -913,6 +923,16 @@ void hzo_rhs(const hzo_grid* g, const hzo_opts* o, const double* met, const doub
   std::vector<double> Lv;
   rhs(M, *o, met, prim, Lv);
   std::memcpy(L, Lv.data(), sizeof(double) * Lv.size());
+}
+
+// The metric source and cleaning damping of the grid alone (the part of hzo_rhs that is not a
+// flux difference), field-major; zero for the fields without a source.  For tests.
+void hzo_rhs_source(const hzo_grid* g, const hzo_opts* o, const double* met, const double* prim,
+                    double* S) {
+  Mesh M(*g);
+  std::vector<double> Sv((size_t)M.ncell * NCONS, 0.0);
+  add_sources(M, *o, met, prim, Sv);
+  std::memcpy(S, Sv.data(), sizeof(double) * Sv.size());
 }
 
 // The CFL rate: max over cells of the sum over active axes of max(|l+|, |l-|) / dx_d (with the
