@@ -14,6 +14,14 @@ from paper_1102_5202_gb300 import workloads as W
 TOL_ONE_STEP = 1e-10
 TOL_END = 1e-8
 
+# End-time bar where the workload itself amplifies rounding: the GPU result may differ from the
+# oracle's by at most this factor times the oracle's own spread, the largest relative L1 per
+# field between the oracle run and the oracle runs from one-ulp perturbations of its input (the
+# same steps).  A discrete decision (the atmosphere threshold, a limiter or monotonicity switch)
+# that an ulp flips turns rounding into an O(1) change of one cell, which then spreads; which
+# perturbation flips which decision first is chance, so several perturbations are taken.
+SPREAD_FACTOR = 10.0
+
 
 def oracle_setup(P):
     grid = O.make_grid(P.n, P.dx, P.bc)
@@ -133,3 +141,57 @@ def general_metric(X, Y, Z):
     m[6] = -0.015 * np.sin(2 * math.pi * Y)
     m[8] = 0.01 * np.cos(2 * math.pi * X)
     return m
+
+
+def perturbed(P, kind: str, seed: int = 5):
+    """P with its primitive input moved by one ulp: 'rho' up, 'p' down, or 'all' (every
+    field, in a seeded random direction)."""
+    import dataclasses
+
+    prim = P.prim.copy()
+    if kind == "rho":
+        prim[0] = np.nextafter(prim[0], np.inf)
+    elif kind == "p":
+        prim[1] = np.nextafter(prim[1], -np.inf)
+    elif kind == "all":
+        rng = np.random.Generator(np.random.PCG64(seed))
+        prim = np.nextafter(prim, rng.choice([-np.inf, np.inf], size=prim.shape))
+    else:
+        raise ValueError(kind)
+    return dataclasses.replace(P, prim=prim)
+
+
+def oracle_replay(P, dts):
+    """The oracle from P's input over the given time steps: (prim, cons)."""
+    grid, opts = oracle_setup(P)
+    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
+    prim = P.prim
+    for dt in dts:
+        prim, U, _ = O.step(grid, opts, P.metric, prim, U, dt)
+    return prim, U
+
+
+def integral_diff(a, b):
+    """|sum a_f - sum b_f| / sum |b_f| per conserved field over the grid."""
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.abs(a.sum(axis=1) - b.sum(axis=1)) / np.maximum(np.abs(b).sum(axis=1), 1e-300)
+
+
+def oracle_spread(P, ref_prim, run, kinds=("rho", "p", "all")):
+    """The oracle's own spread on this case: the largest relative L1 per field between
+    ref_prim (the oracle run from P) and run(Q) for the one-ulp perturbations Q of P."""
+    spread = np.zeros(ref_prim.shape[0])
+    for kind in kinds:
+        spread = np.maximum(spread, rel_l1(run(perturbed(P, kind)), ref_prim))
+    return spread
+
+
+def assert_within_spread(gpu, orc, spread, what="", fields=None):
+    """GPU vs oracle per field within max(TOL_END, SPREAD_FACTOR x the oracle's spread)."""
+    r = rel_l1(gpu, orc)
+    bar = np.maximum(TOL_END, SPREAD_FACTOR * spread)
+    idx = range(gpu.shape[0]) if fields is None else fields
+    bad = [(W.PRIM_FIELDS[f], float(r[f]), float(bar[f])) for f in idx if not (r[f] <= bar[f])]
+    assert not bad, f"{what}: relative L1 above the spread bar (field, got, bar): {bad}"
+    return r, bar

@@ -49,33 +49,31 @@ def test_mixed_tube_one_step_and_end(case):
 
 
 def test_mixed_blob_one_and_five_steps():
-    """At the surface of the blob the gas is cold (p/rho down to 1e-10), so its internal energy
-    is below the FP32 resolution of the energy flux: a few surface cells can fail the recovery
-    in mixed precision and are reset to the atmosphere.  They stay rare (<= 1e-3 of the cells)
-    and the field errors stay within the stated bound."""
+    """The blob at 40^3 after one and five steps, every field over the whole grid and over the
+    star's bulk (rho > 0.1 rho_max).  Measured (relative L1 per field, rho p u~x u~y u~z Bx By Bz
+    psi): whole grid after one step 7.8e-7 1.5e-7 3.3e-3 3.9e-3 2.4e-4 1.4e-5 1.4e-5 1.8e-5
+    6.3e-4, after five 6.4e-6 1.8e-6 3.6e-3 3.4e-3 9.0e-4 2.1e-5 1.9e-5 2.0e-5 6.3e-4; bulk
+    <= 1.2e-5 (psi 1.8e-4).  The whole-grid velocity error sits in the near-vacuum cells next to
+    the surface (rho 1e-11 .. 1e-7 beside 1e-4): the FP32 face arithmetic resolves the dense
+    neighbour's momentum flux to 6e-8 of itself, which in a cell 1e4 .. 1e7 times less dense is
+    a velocity change of order one.  It is the FP32 faces' own error, not conditioning: the
+    oracle run from the FP32-rounded input differs from the oracle by <= 4e-8 in u~."""
     P = W.blob3d(40)
     dt = _dt(P)
-    # whole grid: the error sits in the ~200 near-vacuum cells next to the surface (rho 1e-11 to
-    # 1e-7 beside rho 1e-4), where the FP32 rounding of the dense side's HLLE terms is as large
-    # as the cell's own momentum; inside the star the FP32 path is accurate to ~1e-6
-    # Over the whole grid only rho and p are compared: tenuous gas just above the atmosphere
-    # threshold expands into the near vacuum and reaches Lorentz factors of tens within a few
-    # steps in the FP64 oracle as well; its velocity is chaotic under any rounding difference.
-    bound = {1: np.array([1e-5, 1e-5]), 5: np.array([1e-4, 1e-4])}
+    whole = {1: np.array([1e-5, 1e-5, 1e-2, 1e-2, 1e-2, 1e-4, 1e-4, 1e-4, 5e-3]),
+             5: np.array([1e-4, 1e-4, 1e-2, 1e-2, 1e-2, 1e-4, 1e-4, 1e-4, 5e-3])}
+    bulk = {1: np.array([1e-6, 1e-6, 5e-6, 5e-6, 5e-6, 1e-4, 1e-4, 2e-4, 1e-2]),
+            5: np.array([1e-4, 1e-4, 2e-4, 2e-4, 2e-4, 1e-3, 1e-3, 1e-3, 5e-2])}
     for nsteps in (1, 5):
         gp, gc, gs = gpu_run(P, nsteps=nsteps, dt=dt, solver=_mixed(P))
         op, oc, _ = oracle_run(P, nsteps=nsteps, dt=dt)
         # failed recoveries (cells reset to the atmosphere), counted over all substeps
         assert gs["fails"] <= 1e-3 * P.ncell * 3 * nsteps
         r = rel_l1(gp, op)
-        assert np.all(r[:2] <= bound[nsteps]), (nsteps, r)
-        # the star's bulk: rho > 0.1 rho_max; B and psi carry the truncation-level divergence
-        # error of the field's kink at p = 0.04 p_max, so their relative errors are larger
+        assert np.all(r <= whole[nsteps]), (nsteps, r)
         star = op[0] > 0.1 * op[0].max()
         ri = rel_l1(gp[:, star][:, None, None, :], op[:, star][:, None, None, :])
-        bulk = {1: np.array([1e-6, 1e-6, 5e-6, 5e-6, 5e-6, 1e-4, 1e-4, 2e-4, 1e-2]),
-                5: np.array([1e-4, 1e-4, 2e-4, 2e-4, 2e-4, 1e-3, 1e-3, 1e-3, 5e-2])}[nsteps]
-        assert np.all(ri <= bulk), (nsteps, ri)
+        assert np.all(ri <= bulk[nsteps]), (nsteps, ri)
         print(f"blob40 mixed vs FP64 oracle after {nsteps} step(s): all cells "
               f"{np.array2string(r, precision=1)}; star bulk (rho > 0.1 max) {np.array2string(ri, precision=1)}")
 
@@ -104,44 +102,3 @@ def test_diag_and_general_kernels_agree():
     a, _, _ = gpu_run(P, nsteps=2, dt=dt)
     b, _, _ = gpu_run(Q, nsteps=2, dt=dt)
     assert np.all(rel_l1(a, b) <= 1e-12)
-
-
-def test_mixed_error_statement_96_100_steps():
-    """The error statement of the mixed configuration at the oracle's size: blob 96^3, 100 CFL
-    steps (the FP64 run's time steps replayed by the mixed run and the oracle), relative L1 per
-    field.  Measured: FP64 GPU vs oracle <= 7e-12 in every field; mixed vs oracle, whole grid
-    rho 1.2e-5, p 3.7e-6, u~ 3e-5..9e-5, B 1.9e-5, psi 2.4e-4; star bulk (rho > 0.1 max) 2e-6..4e-6,
-    psi 2.6e-5."""
-    import torch
-
-    P = W.blob3d(96)
-    s64 = hzn.Solver.for_problem(P)
-    dts = []
-    for _ in range(100):
-        s64.step_cfl(0.5, 1e30)
-        dts.append(s64.stats().dt)
-    g64 = s64.primitives().cpu().numpy()
-    assert s64.stats().c2p_failures == 0
-    s64.close()
-    s32 = _mixed(P)
-    for dt in dts:
-        s32.step(dt)
-    g32 = s32.primitives().cpu().numpy()
-    assert s32.stats().c2p_failures == 0
-    s32.close()
-    torch.cuda.synchronize()
-    grid, opts = oracle_setup(P)
-    U = O.grid_prim2cons(grid, opts, P.metric, P.prim)
-    op = P.prim
-    for dt in dts:
-        op, U, nf = O.step(grid, opts, P.metric, op, U, dt)
-        assert nf == 0
-    r64 = rel_l1(g64, op)
-    assert np.all(r64 <= 1e-10), r64
-    r = rel_l1(g32, op)
-    assert np.all(r <= np.array([5e-5, 2e-5, 3e-4, 3e-4, 2e-4, 1e-4, 1e-4, 1e-4, 1e-3])), r
-    star = g64[0] > 0.1 * g64[0].max()
-    rs = rel_l1(g32[:, star][:, None, None, :], op[:, star][:, None, None, :])
-    assert np.all(rs <= np.array([2e-5] * 8 + [2e-4])), rs
-    print(f"blob 96^3, 100 steps: FP64 GPU vs oracle max {r64.max():.1e}; mixed vs oracle whole grid "
-          f"{np.array2string(r, precision=1)}; star bulk {np.array2string(rs, precision=1)}")

@@ -2,12 +2,15 @@
 recovery scheme, and the toroidal-field initial data of §5.2 on the synthetic blob.
 
 The tolerances are the FP64 ones of the benchmark statement (relative L1 per field, 1e-10
-after one step, 1e-8 at the end of a run).  The two recovery schemes reach the same root, so
+after one step, 1e-8 at the end of a run), except where the oracle's own spread under a one-ulp
+change of its input is of that size (PPM on Balsara 1): there the end-of-run bar is a multiple
+of that spread.  The two recovery schemes reach the same root, so
 the 1D and 2D GPU runs also agree with each other to round-off."""
 import numpy as np
 import pytest
 
-from parity import TOL_END, TOL_ONE_STEP, assert_parity, gpu_run, oracle_run, oracle_setup, rel_l1
+from parity import (TOL_END, TOL_ONE_STEP, assert_parity, assert_within_spread, gpu_run,
+                    oracle_run, oracle_setup, oracle_spread, rel_l1)
 from paper_1102_5202_gb300 import hzn
 from paper_1102_5202_gb300 import workloads as W
 import oracle as O
@@ -32,15 +35,13 @@ def _ppm(P):
     return P
 
 
-# End-of-run bar of the PPM tubes.  PPM's monotonicity tests switch on products of neighbour
-# differences, so over 300 steps they amplify rounding-level differences between the two sides
-# more than MC does: Balsara 1 ends at 7e-9 with one evaluation order of the wave speeds and at
-# 1.15e-8 with another that differs by an ulp (Sod: 2.5e-10).  One step stays at 1e-10.
-TOL_END_PPM = 3e-8
-
-
 @pytest.mark.parametrize("case", ["balsara1", "sod"])
 def test_ppm_tubes_one_step_and_end(case):
+    """One step at the FP64 bar; at t = 0.4 (about 300 steps) within SPREAD_FACTOR x the
+    oracle's own spread.  PPM's monotonicity constraints switch on products of neighbour
+    differences, so rounding-level differences flip them in the compound waves of Balsara 1:
+    the oracle run from the input with rho +1 ulp (p -1 ulp) differs from the oracle by 7.3e-9
+    (2.3e-9) in u~x at t = 0.4, and the GPU by 1.0e-8; Sod's spread is 4e-10 (GPU 2.4e-10)."""
     P = _ppm(W.balsara1(400) if case == "balsara1" else W.sod(400))
     dt = _dt(P)
     gp, _, gs = gpu_run(P, nsteps=1, dt=dt)
@@ -50,8 +51,10 @@ def test_ppm_tubes_one_step_and_end(case):
     gp, _, gs = gpu_run(P, t_end=0.4, cfl=0.5)
     op, _, os_ = oracle_run(P, t_end=0.4, cfl=0.5)
     assert gs["steps"] == os_["steps"]
-    r = assert_parity(gp, op, TOL_END_PPM, fields=range(8), what=f"{case} PPM t=0.4")
-    print(f"{case} PPM vs oracle at t=0.4 ({gs['steps']} steps): worst field rel L1 {r[:8].max():.1e}")
+    spread = oracle_spread(P, op, lambda Q: oracle_run(Q, t_end=0.4, cfl=0.5)[0], kinds=("rho", "p"))
+    r, bar = assert_within_spread(gp, op, spread, what=f"{case} PPM t=0.4", fields=range(8))
+    print(f"{case} PPM vs oracle at t=0.4 ({gs['steps']} steps): {np.array2string(r[:8], precision=1)}; "
+          f"oracle spread {np.array2string(spread[:8], precision=1)}")
 
 
 def test_ppm_blob_with_cleaning():
@@ -95,8 +98,9 @@ def test_ppm_mixed_precision_error_bound():
     op, _, _ = oracle_run(P, t_end=0.4, cfl=0.5)
     r = rel_l1(gp, op)
     assert np.all(r[:8] <= 5e-3), r
-    print(f"balsara1 PPM mixed vs FP64 oracle: 1 step {np.array2string(r1[:8], precision=1)}; "
-          f"t=0.4 {np.array2string(r[:8], precision=1)}")
+    fmt = {"float_kind": lambda v: f"{v:.1e}"}
+    print(f"balsara1 PPM mixed vs FP64 oracle: 1 step {np.array2string(r1[:8], formatter=fmt)}; "
+          f"t=0.4 {np.array2string(r[:8], formatter=fmt)}")
 
 
 def test_ppm_rejected_on_too_small_axis_and_by_the_adjoint():
