@@ -279,7 +279,12 @@ int hz_adjoint_backward(hz_adjoint* adj, const double* d_gprim_out, const double
  *     overlaps (two streams, or two host threads) race on the array and give wrong results:
  *     serialise them.
  *   - Arguments and layouts are those of hz_set_metric / hz_set_primitives /
- *     hz_get_primitives; all work is enqueued on stream.  No statistics are returned. */
+ *     hz_get_primitives; the work runs on stream.  The call synchronises the stream twice:
+ *     after the metric scan (it reads back the metric class to choose the kernels, as
+ *     hz_set_metric does) and at the end, so it returns with d_prim_out written.
+ *   - Returns HZ_OK, or HZ_WARN_C2P when the recovery failed in some cells during the run
+ *     (those cells were reset to the atmosphere, as hz_get_stats reports for a context);
+ *     HZ_ERR_ARG, HZ_ERR_TOO_LARGE, HZ_ERR_UNSUPPORTED or HZ_ERR_CUDA otherwise. */
 #define HZ_NOALLOC_SCRATCH_BYTES (16u << 20)
 int hz_step_noalloc(const hz_grid* grid, const hz_options* opts, const double* d_metric,
                     const double* d_prim_in, double* d_prim_out, double dt, int nsteps,
@@ -299,6 +304,14 @@ int hz_step_noalloc(const hz_grid* grid, const hz_options* opts, const double* d
 #define HZ_DW_NRESULTS 9
 int hz_dw_selftest(const double* d_a, const double* d_b, double* d_out, long long n,
                    void* stream);
+
+/* ---- Self-test of the FP64 reciprocal of the FP64 kernels --------------------------------
+ * Not a step of the method: d_out[i] = the reciprocal of d_x[i] as the FP64 kernels form it
+ * (the hardware approximation refined by two Newton-Raphson steps, r <- r + r (1 - x r)), so
+ * that its error against the correctly rounded 1/x can be checked.  Defined for normal x whose
+ * reciprocal is normal.  d_x, d_out: n doubles of caller-owned device memory; work enqueued on
+ * stream.  Returns HZ_ERR_ARG for null pointers or n < 0, HZ_ERR_CUDA if the launch fails. */
+int hz_rcp_selftest(const double* d_x, double* d_out, long long n, void* stream);
 
 #ifdef __cplusplus
 }

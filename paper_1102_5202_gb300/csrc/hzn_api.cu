@@ -383,8 +383,9 @@ int hz_set_primitives(hz_ctx* c, const double* d_prim) {
   launch_pack_in(c, d_prim, c->P[0]);
   launch_prim2cons(c->v, c->kp, c->P[0], c->met, c->U0, c->st);
   // the second primitive buffer and U1 start as copies so that inactive fields stay defined
-  cudaMemcpyAsync(c->P[1], c->P[0], L.p_bytes, cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(c->U1, c->U0, L.u_bytes, cudaMemcpyDeviceToDevice, c->st);
+  cudaError_t e = cudaMemcpyAsync(c->P[1], c->P[0], L.p_bytes, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->U1, c->U0, L.u_bytes, cudaMemcpyDeviceToDevice, c->st);
+  if (e != cudaSuccess) return HZ_ERR_CUDA;
   k_reset_scalars<<<1, 1, 0, c->st>>>(c->sc);
   launch_max_speed(c->v, c->kp, c->P[0], c->met, c->sc, c->st);
   c->have_prim = 1;
@@ -502,5 +503,11 @@ extern "C" int hz_step_noalloc(const hz_grid* grid, const hz_options* opts, cons
   if ((e = hz_set_primitives(&c, d_prim_in)) != HZ_OK) return e;
   for (int s = 0; s < nsteps; ++s)
     if ((e = hz_step(&c, dt)) != HZ_OK) return e;
-  return hz_get_primitives(&c, d_prim_out);
+  if ((e = hz_get_primitives(&c, d_prim_out)) != HZ_OK) return e;
+  // wait for the result and report failed recoveries, as hz_get_stats does
+  unsigned long long fails = 0;
+  cudaError_t ce = cudaMemcpyAsync(&fails, &c.sc->fails, sizeof(fails), cudaMemcpyDeviceToHost, c.st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c.st);
+  if (ce != cudaSuccess) return HZ_ERR_CUDA;
+  return fails ? HZ_WARN_C2P : HZ_OK;
 }

@@ -1,5 +1,6 @@
-// Self-test entry of the double-word arithmetic used by the HZ_FP64_DW kernels (see hzn.h):
-// the same split, operations and half MC slope, applied to caller-given doubles.
+// Self-test entries (see hzn.h): the double-word arithmetic used by the HZ_FP64_DW kernels (the
+// same split, operations and half MC slope, applied to caller-given doubles), and the FP64
+// reciprocal of the FP64 kernels (rcp_fast).
 #include <cuda_runtime.h>
 
 #include "hzn.h"
@@ -33,7 +34,25 @@ __global__ void k_dw_selftest(const double* __restrict__ a, const double* __rest
   }
 }
 
+__global__ void k_rcp_selftest(const double* __restrict__ x, double* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = hzn::rcp_fast(x[i]);
+}
+
+int blocks_of(long long n, int threads) {
+  const long long want = (n + threads - 1) / threads;
+  return (int)(want < 4096 ? want : 4096);
+}
+
 }  // namespace
+
+extern "C" int hz_rcp_selftest(const double* d_x, double* d_out, long long n, void* stream) {
+  if (!d_x || !d_out || n < 0) return HZ_ERR_ARG;
+  if (n == 0) return HZ_OK;
+  k_rcp_selftest<<<blocks_of(n, 256), 256, 0, (cudaStream_t)stream>>>(d_x, d_out, n);
+  return cudaGetLastError() == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+}
 
 extern "C" int hz_dw_selftest(const double* d_a, const double* d_b, double* d_out, long long n,
                               void* stream) {

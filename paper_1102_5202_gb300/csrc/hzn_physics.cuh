@@ -137,9 +137,11 @@ __device__ __forceinline__ void geo_store(double* __restrict__ g, long long off,
   g[9 * ms + off] = G.sqrtmg;
 }
 
-// 1/x from the hardware reciprocal approximation refined by two Newton steps (each doubles the
-// correct bits; the result is within a few ulps of 1/x): a few FP64 instructions fewer than the
-// correctly rounded quotient.  x must be a normal number.  float: the plain quotient.
+// 1/x from the hardware reciprocal approximation (rcp.approx.ftz.f64) refined by two steps of
+// the Newton-Raphson iteration for the reciprocal, r <- r + r (1 - x r) (Newton's method on
+// f(r) = 1/r - x; each step squares the relative error, so the approximation's error falls to
+// a few ulps): a few FP64 instructions fewer than the correctly rounded quotient.  x must be a
+// normal number.  float: the plain quotient.
 __device__ __forceinline__ double rcp_fast(double x) {
 #ifdef __CUDA_ARCH__
   double r;

@@ -32,6 +32,7 @@ EXPORTED = (
     "hz_workspace_bytes", "hz_create", "hz_destroy", "hz_set_metric", "hz_set_primitives",
     "hz_get_primitives", "hz_get_conserved", "hz_step", "hz_step_cfl", "hz_max_speed",
     "hz_get_stats", "hz_strerror", "hz_version", "hz_step_noalloc", "hz_dw_selftest",
+    "hz_rcp_selftest",
 )
 HZ_DW_NRESULTS = 9
 
@@ -108,6 +109,7 @@ def lib():
             L.hz_step_noalloc.argtypes = [P(hz_grid), P(hz_options), vp, vp, vp, ctypes.c_double,
                                           ctypes.c_int, vp]
             L.hz_dw_selftest.argtypes = [vp, vp, vp, ctypes.c_longlong, vp]
+            L.hz_rcp_selftest.argtypes = [vp, vp, ctypes.c_longlong, vp]
             L.hz_strerror.argtypes = [ctypes.c_int]
             L.hz_strerror.restype = ctypes.c_char_p
             L.hz_version.restype = ctypes.c_int
@@ -136,6 +138,16 @@ def hz_dw_selftest(a, b):
     out = torch.empty((HZ_DW_NRESULTS, 2, n), dtype=torch.float64, device=a.device)
     st = torch.cuda.current_stream(a.device).cuda_stream
     _check(lib().hz_dw_selftest(a.data_ptr(), b.data_ptr(), out.data_ptr(), n, st), "hz_dw_selftest")
+    return out
+
+
+def hz_rcp_selftest(x):
+    """The FP64 kernels' reciprocal of each element of x (a 1-D float64 CUDA tensor)."""
+    import torch
+
+    out = torch.empty_like(x)
+    st = torch.cuda.current_stream(x.device).cuda_stream
+    _check(lib().hz_rcp_selftest(x.data_ptr(), out.data_ptr(), int(x.numel()), st), "hz_rcp_selftest")
     return out
 
 
@@ -196,9 +208,11 @@ def hz_get_stats(ctx: int) -> hz_stats:
 
 
 def hz_step_noalloc(grid: hz_grid, opts: hz_options, d_metric: int, d_prim_in: int, d_prim_out: int,
-                    dt: float, nsteps: int, stream: int) -> None:
-    """nsteps fixed-dt RK3 steps with the library's static scratch (no allocation at all)."""
-    _check(lib().hz_step_noalloc(ctypes.byref(grid), ctypes.byref(opts), ctypes.c_void_p(d_metric),
+                    dt: float, nsteps: int, stream: int) -> int:
+    """nsteps fixed-dt RK3 steps with the library's static scratch (no allocation at all).
+    Returns HZ_OK or HZ_WARN_C2P (failed recoveries reset to the atmosphere); the output is
+    written when the call returns."""
+    return _check(lib().hz_step_noalloc(ctypes.byref(grid), ctypes.byref(opts), ctypes.c_void_p(d_metric),
                                  ctypes.c_void_p(d_prim_in), ctypes.c_void_p(d_prim_out), float(dt),
                                  int(nsteps), ctypes.c_void_p(stream)), "hz_step_noalloc")
 

@@ -219,3 +219,21 @@ def test_state_calls_out_of_order():
     assert e.value.code == hzn.HZ_ERR_STATE
     with pytest.raises(hzn.HznError):
         s.set_primitives(np.zeros((9, 1, 1, 16)))  # metric first
+
+
+def test_fp64_reciprocal_error_bound():
+    """The FP64 kernels' reciprocal (hardware approximation + two Newton-Raphson steps) against
+    the correctly rounded 1/x over normal x of both signs across the exponent range, and on
+    powers of two (exact): within 2 ulps."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(91))
+    e = rng.uniform(-1000.0, 1000.0, 200000)
+    x = np.ldexp(rng.uniform(1.0, 2.0, e.size), e.astype(np.int64)) * rng.choice([-1.0, 1.0], e.size)
+    x = np.concatenate([x, np.ldexp(1.0, np.arange(-1000, 1001)), [1.0, -1.0, 3.0, 1.0 / 3.0]])
+    got = hzn.hz_rcp_selftest(torch.tensor(x, device="cuda")).cpu().numpy()
+    want = 1.0 / x
+    ulps = np.abs(got - want) / np.spacing(np.abs(want))
+    assert ulps.max() <= 2.0, ulps.max()
+    p2 = np.ldexp(1.0, np.arange(-1000, 1001))
+    assert np.all(hzn.hz_rcp_selftest(torch.tensor(p2, device="cuda")).cpu().numpy() == 1.0 / p2)

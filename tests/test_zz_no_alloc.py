@@ -40,9 +40,13 @@ def _noalloc(P, opts, dt, nsteps, stream):
     pin = torch.from_numpy(np.ascontiguousarray(P.prim)).cuda()
     pout = torch.full_like(pin, float("nan"))
     grid = hzn.make_grid(P.n, P.dx, P.bc)
-    hzn.hz_step_noalloc(grid, opts, met.data_ptr(), pin.data_ptr(), pout.data_ptr(), dt, nsteps,
-                        stream.cuda_stream)
     torch.cuda.synchronize()
+    code = hzn.hz_step_noalloc(grid, opts, met.data_ptr(), pin.data_ptr(), pout.data_ptr(), dt,
+                               nsteps, stream.cuda_stream)
+    # the call returns once its result is written: nothing of it is left on the stream, and no
+    # recovery failed on these problems
+    assert stream.query()
+    assert code == hzn.HZ_OK
     return pout.cpu().numpy()
 
 
