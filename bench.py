@@ -332,7 +332,6 @@ def run_gpu(args, rank, world, local):
             "hbm_roofline": hbm,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "mixed": mixed,
             "ensemble": ensemble,
             "adjoint": adjoint,
             "variants": variants,
@@ -341,6 +340,8 @@ def run_gpu(args, rank, world, local):
             "clocks": clk,
             "c2p_failures": int(st.c2p_failures),
             "sim_time": st.t,
+            # last, so that a reader of the line's tail sees the mixed configuration's figures
+            "mixed": mixed,
         }
         print(json.dumps(line))
     if dist is not None:
@@ -381,14 +382,15 @@ def run_mixed(args, dist, local, hbm_peak):
     del s
     torch.cuda.empty_cache()
     err = mixed_error(P) if args.mixed_error else None
-    return {"value": value, "unit": UNIT, "workload": f"blob3d_{args.n_mixed}^3_mixed_cleaning",
-            "error_vs_fp64_gpu_100_steps": err,
-            "cells": P.ncell, "ms_per_step": seconds / args.steps * 1e3, "dtype": "f32/f64",
-            "roofline": mixed_roofline(P.ncell, substep_s),
+    # the headline figures come last (a reader of the line's tail sees them first)
+    return {"error_vs_fp64_gpu_100_steps": err, "roofline": mixed_roofline(P.ncell, substep_s),
+            "workload": f"blob3d_{args.n_mixed}^3_mixed_cleaning", "cells": P.ncell,
+            "dtype": "f32/f64", "c2p_failures": int(st.c2p_failures), "gpu_launches": 4 * args.steps,
+            "ms_per_step": seconds / args.steps * 1e3,
             "hbm_roofline": {"bytes_per_zu": HBM_BYTES_PER_ZU_MIXED, "achieved": ach, "peak": hbm_peak,
-                             "unit": "GB/s", "frac": ach / hbm_peak,
-                             "roofline_zu_per_s": hbm_peak * 1e9 / HBM_BYTES_PER_ZU_MIXED},
-            "c2p_failures": int(st.c2p_failures), "gpu_launches": 4 * args.steps}
+                             "unit": "GB/s", "roofline_zu_per_s": hbm_peak * 1e9 / HBM_BYTES_PER_ZU_MIXED,
+                             "frac": ach / hbm_peak},
+            "unit": UNIT, "value": value}
 
 
 def mixed_error(P, steps: int = 100):
@@ -712,10 +714,36 @@ def run_cpu_baseline(P, seconds_target=15.0, m=48, m_single=24, seconds_single=6
         steps1, sec1 = _time_oracle_steps(O, Q1, seconds_single)
     finally:
         O.set_num_threads(cores)
-    out["single_thread"] = {"value": Q1.ncell * steps1 / sec1, "unit": UNIT, "cores": 1,
+    v1 = Q1.ncell * steps1 / sec1
+    out["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
                             "sample": f"{steps1} RK3 step(s) of the central {m_single}^3 sub-box, "
                                       f"{sec1:.1f} s"}
+    out["cpu_model"] = cpu_model()
+    # the one-core figure and the CPU also in the sample text, which every reader of the line keeps
+    out["sample"] += (f"; one core: {v1:.3g} {UNIT} on {steps1} RK3 step(s) of the central "
+                      f"{m_single}^3 sub-box; CPU {out['cpu_model']}, {cores} threads")
     return out
+
+
+def cpu_model() -> str:
+    """Model name of the host CPU (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    import subprocess
+
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
 
 
 def run_reference(args, rank, world):

@@ -432,10 +432,12 @@ __device__ __forceinline__ G4<R> g4_at(const KParams& kp, const S* __restrict__ 
 template <bool YA, bool ZA, bool CLEAN, bool DIAG, typename R>
 __device__ __forceinline__ double cell_max_speed(const KParams& kp, const Geom<R>& G, const R P[9],
                                                  const Consts<R>& c) {
+  // FP64: quotients and square roots through rcp_fast and the reciprocal square root
+  constexpr bool FAST = SameType<R, double>::value;
   const State<R> S = make_state<DIAG>(G, P, c);
-  const R c2 = cms2_of(S, c);
+  const R c2 = cms2_of<R, FAST>(S, c);
   R lm, lp;
-  speeds_of<0, DIAG>(G, S, c2, lm, lp);
+  speeds_of<0, DIAG, R, FAST>(G, S, c2, lm, lp);
   double a = (double)fmax(fabs(lm), fabs(lp));
   if (CLEAN) {
     clean_speeds<0, DIAG>(G, c.ch, lm, lp);
@@ -443,7 +445,7 @@ __device__ __forceinline__ double cell_max_speed(const KParams& kp, const Geom<R
   }
   double v = a * kp.idx;
   if (YA) {
-    speeds_of<1, DIAG>(G, S, c2, lm, lp);
+    speeds_of<1, DIAG, R, FAST>(G, S, c2, lm, lp);
     a = (double)fmax(fabs(lm), fabs(lp));
     if (CLEAN) {
       clean_speeds<1, DIAG>(G, c.ch, lm, lp);
@@ -452,7 +454,7 @@ __device__ __forceinline__ double cell_max_speed(const KParams& kp, const Geom<R
     v += a * kp.idy;
   }
   if (ZA) {
-    speeds_of<2, DIAG>(G, S, c2, lm, lp);
+    speeds_of<2, DIAG, R, FAST>(G, S, c2, lm, lp);
     a = (double)fmax(fabs(lm), fabs(lp));
     if (CLEAN) {
       clean_speeds<2, DIAG>(G, c.ch, lm, lp);
@@ -499,7 +501,7 @@ __device__ __forceinline__ void block_stats(DevScalars* sc, double vloc, int nfa
 
 // Recovery with atmosphere / floor handling; rewrites U when the cell is reset.  TG, TP: the
 // element types of the guess and of the result (float for the mixed path, whose primitive
-// state is stored in FP32; a reset recomputes U from that stored state).
+// state is stored in FP32; a pressure-floor reset recomputes U from that stored state).
 template <bool CLEAN, bool DIAG, bool ONE_FINISH = false, typename TG = double, typename TP = double>
 __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G, double U[9],
                                        const TG Pg[9], const Consts<double>& c, TP P[9],
@@ -511,22 +513,36 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
   if (!atm)
     r = con2prim<CLEAN, DIAG, ONE_FINISH, TG, TP>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_step_tol, P, kp.c2p_1d);
   iters = r.iters;
-  bool reset = false;
   if (atm || !r.ok || (double)P[P_RHO] < kp.rho_floor) {
-    const double isg = 1.0 / G.sqrtmg;
-    P[P_BX] = (TP)(U[U_BX] * isg);
-    P[P_BY] = (TP)(U[U_BY] * isg);
-    P[P_BZ] = (TP)(U[U_BZ] * isg);
-    P[P_PSI] = CLEAN ? (TP)(U[U_PSI] / G.sqrtg) : TP(0);
+    // The atmosphere state: rho_floor, p_atm, u~ = 0, the cell's B and psi.  Its conserved
+    // vector in closed form: u~ = 0 gives W = 1, u^t = 1/alpha, u_i = 0 and b^t = 0, hence
+    // b^i = alpha B^i and b^2 = gamma_ij Bn^i Bn^j with the Eulerian field Bn^i = alpha B^i =
+    // U_B^i / sqrt(gamma), and U = (sqrt(gamma) rho, -sqrt(-g) (rho + p / (gamma - 1) + b^2/2),
+    // 0, 0, 0, U_B, U_Psi): the value make_state + cons_of give for that state (§2.1).
+    const double isg = rcp_fast(G.sqrtg);
+    const double bnx = U[U_BX] * isg, bny = U[U_BY] * isg, bnz = U[U_BZ] * isg;
+    double b2;
+    if constexpr (DIAG) {
+      b2 = G.gxx * bnx * bnx + G.gyy * bny * bny + G.gzz * bnz * bnz;
+    } else {
+      b2 = (G.gxx * bnx + 2.0 * (G.gxy * bny + G.gxz * bnz)) * bnx +
+           (G.gyy * bny + 2.0 * G.gyz * bnz) * bny + G.gzz * bnz * bnz;
+    }
+    P[P_BX] = (TP)(bnx * G.ialp);
+    P[P_BY] = (TP)(bny * G.ialp);
+    P[P_BZ] = (TP)(bnz * G.ialp);
+    P[P_PSI] = CLEAN ? (TP)(U[U_PSI] * isg) : TP(0);
     P[P_RHO] = (TP)kp.rho_floor;
     P[P_PRS] = (TP)kp.p_atm;
     P[P_UX] = P[P_UY] = P[P_UZ] = TP(0);
-    reset = true;
+    // rest-mass plus internal energy density of the atmosphere: rho + p / (gamma - 1), with
+    // 1 / (gamma - 1) = gamma / (gamma - 1) - 1
+    const double e_atm = fma(kp.p_atm, kp.gfac - 1.0, kp.rho_floor);
+    U[U_D] = G.sqrtg * kp.rho_floor;
+    U[U_TT] = -G.sqrtmg * fma(0.5, b2, e_atm);
+    U[U_TX] = U[U_TY] = U[U_TZ] = 0.0;
   } else if ((double)P[P_PRS] < kp.p_floor) {
     P[P_PRS] = (TP)kp.p_floor;
-    reset = true;
-  }
-  if (reset) {
     double Pd[9];
 #pragma unroll
     for (int f = 0; f < 9; ++f) Pd[f] = (double)P[f];

@@ -341,16 +341,20 @@ __device__ __forceinline__ R tdg(const Tup<R>& T, const G4<R>& gp, const G4<R>& 
 
 // Squared fast-magnetosonic speed c^2 = cs^2 + vA^2 - cs^2 vA^2 with cs^2 = gamma p / w and
 // vA^2 = b^2 / (w + b^2), written over one common denominator.
-template <typename R>
+// FAST (FP64 only): the quotient through rcp_fast (within a few ulps of the correctly rounded one).
+template <typename R, bool FAST = false>
 __device__ __forceinline__ R cms2_of(const State<R>& S, const Consts<R>& c) {
   const R gp = c.gamma * S.p;
   const R wt = S.w + S.b2;
-  return (gp * wt + S.b2 * (S.w - gp)) / (S.w * wt);
+  if constexpr (FAST) return (gp * wt + S.b2 * (S.w - gp)) * rcp_fast(S.w * wt);
+  else return (gp * wt + S.b2 * (S.w - gp)) / (S.w * wt);
 }
 
 // Characteristic speeds along D: roots of A l^2 + B l + C = 0 from the dispersion relation
 // (u^D - l u^t)^2 = c^2 [g^tt l^2 - 2 g^tD l + g^DD + (u^D - l u^t)^2].
-template <int D, bool DIAG, typename R>
+// FAST (FP64 only): the square root as disc / sqrt(disc) through the reciprocal square root and
+// 1 / (2A) through rcp_fast (each within a few ulps of the correctly rounded value).
+template <int D, bool DIAG, typename R, bool FAST = false>
 __device__ __forceinline__ void speeds_of(const Geom<R>& G, const State<R>& S, R c2, R& lm, R& lp) {
   const R ia2 = G.ialp * G.ialp;
   const R ud = sel<D>(S.ux, S.uy, S.uz);
@@ -369,8 +373,14 @@ __device__ __forceinline__ void speeds_of(const Geom<R>& G, const State<R>& S, R
   }
   R disc = B * B - R(4) * A * C;
   disc = disc > R(0) ? disc : R(0);
-  const R sq = sqrt(disc);
-  const R i2a = R(0.5) / A;
+  R sq, i2a;
+  if constexpr (FAST) {
+    sq = disc > R(0) ? disc * rsqrt(disc) : R(0);
+    i2a = R(0.5) * rcp_fast(A);
+  } else {
+    sq = sqrt(disc);
+    i2a = R(0.5) / A;
+  }
   lp = (-B + sq) * i2a;
   lm = (-B - sq) * i2a;
 }
@@ -617,6 +627,66 @@ static __device__ __noinline__ bool c2p_bracketed(const C2PScalars q, double zgu
   return true;
 }
 
+// sqrt(a) to FP64 accuracy from the FP32 square root of a nearby float af: two steps of Heron's
+// iteration s <- s + (a - s^2) / (2 s), with 1 / (2 s) kept at its FP32 value (each step
+// multiplies the relative error by about the FP32 root's, 2^-24).  Four FP64 instructions and
+// two conversions instead of a correctly rounded FP64 square root.  a > 0, af > 0.
+__device__ __forceinline__ double sqrt_from_f32(double a, float af) {
+  const float s = sqrtf(af);
+  const double sd = (double)s, h = (double)(0.5f / s);
+  double r = fma(fma(-sd, sd, a), h, sd);
+  return fma(fma(-r, r, a), h, r);
+}
+
+// Inverse of the recovery's 2x2 Jacobian (the derivatives of r1, r2 of c2p_newton) formed in
+// FP32 at an FP32 root (zf, vf).
+struct C2PJac32 {
+  float a11, a12, a21, a22;  // J^-1
+  float iz2;                 // 1 / zf^2
+};
+
+__device__ __forceinline__ C2PJac32 c2p_jac32(float zf, float vf, float bf, float qf, float gf) {
+  const float omf = 1.0f - vf;
+  const float rs = rsqrtf(omf);
+  const float iz = 1.0f / zf;
+  const float iz2 = iz * iz;
+  const float zbf = zf + bf;
+  const float j11 = 2.0f * zbf * vf + 2.0f * qf * zbf * iz2 * iz;
+  const float j12 = zbf * zbf;
+  const float j21 = 1.0f - gf * omf + qf * iz2 * iz;
+  const float j22 = gf * (zf - 0.5f * rs) + 0.5f * bf;
+  const float idet = 1.0f / (j11 * j22 - j12 * j21);
+  C2PJac32 J;
+  J.a11 = j22 * idet;
+  J.a12 = -j12 * idet;
+  J.a21 = -j21 * idet;
+  J.a22 = j11 * idet;
+  J.iz2 = iz2;
+  return J;
+}
+
+// One correction of a root (z, v^2) of the recovery equations: the residuals are formed in FP64
+// (they are differences of nearly equal O(1) terms, the pressure above all), multiplied through
+// by z^2 so that they need no FP64 division,
+//   R1 = z^2 ((z + b)^2 v^2 - s) - q (2z + b),   R2 = z^2 (z - p + b (1 + v^2)/2 - e) - q / 2,
+// and the step -J^-1 (R1, R2) / z^2 is taken with the FP32 Jacobian J of an FP32 root nearby.
+// Each correction multiplies the error by about J's relative error (2^-24): one takes an FP32
+// root to the accuracy of a full FP64 Newton step from it, two to FP64 accuracy.  om_seed is
+// 1 - v^2 in FP32 (seed of the FP64 square root).  Writes the step (dz, dv).
+__device__ __forceinline__ void c2p_correct(const C2PScalars& q, const C2PJac32& J, float om_seed,
+                                            double z, double v2, float& dz, float& dv) {
+  const double om = 1.0 - v2;
+  const double sq = sqrt_from_f32(om, om_seed);
+  const double z2 = z * z, zb = z + q.b;
+  const double R1 = fma(z2, fma(zb * zb, v2, -q.s), -q.q * fma(2.0, z, q.b));
+  const double p = q.g1 * fma(z, om, -sq);
+  const double hb = 0.5 * q.b;
+  const double R2 = fma(z2, ((z - p) + fma(hb, v2, hb)) - q.e, -0.5 * q.q);
+  const float r1 = (float)R1 * J.iz2, r2 = (float)R2 * J.iz2;
+  dz = -(J.a11 * r1 + J.a12 * r2);
+  dv = -(J.a21 * r1 + J.a22 * r2);
+}
+
 // Guarded Newton update: keep z > 0 and 0 <= v^2 < 1.  Returns false when the step had to be
 // replaced by halving the distance to the bound z = 0 or v^2 = 1: a run of such steps shrinks
 // geometrically without converging, so it may not end the iteration.  A step below v^2 = 0 is
@@ -698,7 +768,8 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
   q.g1 = g1;
 
   // initial guess from the previous primitive state: z = w W^2 / D, v^2 = uu / (1 + uu)
-  double z, v2;
+  double z = 0.0, v2 = 0.0;
+  float zg32 = 0.f, vg32 = 0.f;  // ONE_FINISH: the guess stays in FP32
   {
     using T = TG;
     const T vx = Pg[P_UX], vy = Pg[P_UY], vz = Pg[P_UZ];
@@ -709,19 +780,30 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
            ((T)G.gxy * vx + (T)G.gyy * vy + (T)G.gyz * vz) * vy +
            ((T)G.gxz * vx + (T)G.gyz * vy + (T)G.gzz * vz) * vz;
     const T wg = Pg[P_RHO] + (T)c.gfac * Pg[P_PRS];
-    z = (double)(wg * (T(1) + uu) * (T)iD);
-    v2 = (double)(uu / (T(1) + uu));
-    if (!(z > 0.0) || !(z < 1e30)) z = q.e;
+    if constexpr (ONE_FINISH) {
+      zg32 = (float)(wg * (T(1) + uu) * (T)iD);
+      vg32 = (float)(uu / (T(1) + uu));
+      if (!(zg32 > 0.f) || !(zg32 < 1e30f)) zg32 = (float)q.e;
+    } else {
+      z = (double)(wg * (T(1) + uu) * (T)iD);
+      v2 = (double)(uu / (T(1) + uu));
+      if (!(z > 0.0) || !(z < 1e30)) z = q.e;
+    }
   }
   bool settled = false;
   bool done = false;
+  float om_seed = -1.f;  // ONE_FINISH: 1 - v^2 in FP32 after the FP64 correction
   if (one_d) {
+    if constexpr (ONE_FINISH) {
+      z = (double)zg32;
+      v2 = (double)vg32;
+    }
     if (!c2p_bracketed(q, z, z, v2, res.iters)) return res;
     done = true;
   }
   // FP32 stage
   if (!done) {
-    float zf = (float)z, vf = (float)v2;
+    float zf = ONE_FINISH ? zg32 : (float)z, vf = ONE_FINISH ? vg32 : (float)v2;
     const float ef = (float)q.e, sf = (float)q.s, qf = (float)q.q, bf = (float)q.b, gf = (float)g1;
     for (int it = 0; it < 30; ++it) {
       const NewtonStep<float> st = c2p_newton<float>(zf, vf, ef, sf, qf, bf, gf);
@@ -732,20 +814,38 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
         break;
       }
     }
-    if (zf > 0.f && vf >= 0.f && vf < 1.f && isfinite(zf)) {
+    const bool valid = zf > 0.f && vf >= 0.f && vf < 1.f && isfinite(zf);
+    if (valid) {
       z = (double)zf;
       v2 = (double)vf;
-    } else {
-      settled = false;
+    } else if constexpr (ONE_FINISH) {
+      z = (double)zg32;
+      v2 = (double)vg32;
+    }
+    // FP64 corrections with the FP32 Jacobian (c2p_correct): one for a result stored in FP32
+    // (ONE_FINISH), until a step falls below step_tol (at most three) otherwise.  The full FP64
+    // Newton iteration below runs only if they do not settle or leave 0 < z, 0 <= v^2 < 1.
+    if (valid && settled) {
+      const C2PJac32 J = c2p_jac32(zf, vf, bf, qf, gf);
+      const float seed = 1.0f - vf;
+      const double tol = ONE_FINISH ? 1e-5 : step_tol;
+      for (int k = 0; k < (ONE_FINISH ? 1 : 3); ++k) {
+        float dz, dv;
+        c2p_correct(q, J, seed, z, v2, dz, dv);
+        ++res.iters;
+        const double zn = z + (double)dz, vn = v2 + (double)dv;
+        if (!(zn > 0.0) || !(vn < 1.0) || !(fabsf(dz) <= 1e-5f * zf) || !(fabsf(dv) <= 1e-5f)) break;
+        z = zn;
+        v2 = vn < 0.0 ? 0.0 : vn;
+        if (fabs((double)dz) <= tol * z && fabs((double)dv) <= tol) {
+          done = true;
+          om_seed = seed - dv;
+          break;
+        }
+      }
     }
   }
   // FP64 stage
-  if (!done && ONE_FINISH && settled) {
-    const NewtonStep<double> st = c2p_newton<double>(z, v2, q.e, q.s, q.q, q.b, g1);
-    const bool plain = c2p_apply(z, v2, st);
-    ++res.iters;
-    done = plain && fabs(st.dz) <= 1e-5 * z && fabs(st.dv) <= 1e-5;
-  }
   for (int it = 0; !done && it < maxit; ++it) {
     const NewtonStep<double> st = c2p_newton<double>(z, v2, q.e, q.s, q.q, q.b, g1);
     const bool plain = c2p_apply(z, v2, st);
@@ -759,11 +859,18 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
     if (!c2p_bracketed(q, z, z, v2, res.iters)) return res;
   }
   const double om = 1.0 - v2;
-  const double W = rsqrt(om);
-  const double rW = om * W;  // 1/W
+  double rW, W = 0.0;  // 1/W = sqrt(1 - v^2), W
+  if constexpr (ONE_FINISH) {
+    if (om_seed < 0.f) om_seed = (float)om;  // after the FP64 iteration
+    rW = sqrt_from_f32(om, om_seed);
+  } else {
+    W = rsqrt(om);
+    rW = om * W;
+  }
   const double Z = z * Dd;
   const double p = g1 * (Z * (1.0 - v2) - Dd * rW);
   if constexpr (sizeof(TP) == sizeof(double)) {
+    if constexpr (ONE_FINISH) W = 1.0 / rW;
     const double iZB = rcp_fast(Z + B2);
     const double sbz = SB * rcp_fast(Z);
     P[P_RHO] = Dd * rW;
@@ -777,7 +884,7 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
     P[P_PSI] = CLEAN ? U[U_PSI] * isg : 0.0;
   } else {
     // result stored in FP32: everything but p from FP32 copies of the FP64 quantities
-    const TP rWf = (TP)rW, Zf = (TP)Z, ia = (TP)G.ialp;
+    const TP rWf = ONE_FINISH ? (TP)sqrtf(om_seed) : (TP)rW, Zf = (TP)Z, ia = (TP)G.ialp;
     const TP Bxf = (TP)Bx, Byf = (TP)By, Bzf = (TP)Bz;
     const TP W = TP(1) / rWf;
     const TP iZB = TP(1) / (Zf + (TP)B2);
