@@ -87,9 +87,10 @@ typedef struct {
   double p_floor;   /* pressure floor                                                    */
   double atm_K;     /* atmosphere pressure = atm_K rho_floor^gamma when > 0, else p_floor */
   int c2p_maxit;    /* Newton iteration cap of the recovery (1 .. 200)                    */
-  double c2p_tol;   /* recovery accuracy (1e-15 .. 1e-6): the FP64 Newton iteration stops
-                       after a step |dZ| <= 0.01 sqrt(c2p_tol) Z (quadratic convergence then
-                       leaves an error below c2p_tol)                                         */
+  double c2p_tol;   /* recovery accuracy (1e-15 .. 1e-6): the FP64 stage (corrections with the
+                       Jacobian of the FP32 root, each of which multiplies the error by about
+                       2^-24; Newton steps if they do not settle) stops after a step
+                       |dZ| <= 0.01 sqrt(c2p_tol) Z, which leaves an error below c2p_tol      */
   int recon;        /* HZ_RECON_MC: TVD with the MC limiter.  HZ_RECON_PPM: the piecewise
                        parabolic method (§3.2; interface parabola from MC-limited slopes, then
                        the monotonicity constraints; no steepening or flattening); needs at

@@ -273,6 +273,7 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   kp.c2p_tol = opts->c2p_tol;
   kp.c2p_step_tol = 0.01 * sqrt(opts->c2p_tol);
   kp.c2p_1d = opts->c2p == HZ_C2P_1D;
+  set_float_consts(kp);
   {
     const int ndims = kp.gx + kp.gy + kp.gz;
     kp.geo_c = geo;

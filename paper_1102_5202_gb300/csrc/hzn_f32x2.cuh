@@ -98,6 +98,30 @@ __device__ __forceinline__ double widen(float f) {
   return E == 0u ? 0.0 : __hiloint2double((int)hw, (int)lw);
 }
 
+// float -> double, exact, by integer operations for finite floats (zero for subnormals, which
+// lie below 1.2e-38); infinities and NaNs take the conversion instruction, so they propagate.
+__device__ __forceinline__ double widen_exact(float f) {
+  if (((__float_as_uint(f) >> 23) & 0xffu) == 0xffu) return (double)f;
+  return widen(f);
+}
+
+// double -> float rounded to nearest (ties to even) by integer operations, for results in the
+// FP32 normal range and for zeros (FP64 subnormals give a signed zero, as the conversion does);
+// results below the FP32 normal range, infinities and NaNs take the conversion instruction.
+__device__ __forceinline__ float narrow(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned E = (hw >> 20) & 0x7ffu;
+  if (E == 0u) return __uint_as_float(hw & 0x80000000u);
+  if (E - 897u > 253u) return (float)x;  // the float is not normal: subnormal, zero, inf, NaN
+  const unsigned m = ((hw & 0xfffffu) << 3) | (lw >> 29);  // the 23 kept mantissa bits
+  const unsigned rest = lw & 0x1fffffffu;                   // the 29 dropped ones
+  unsigned r = ((E - 896u) << 23) | m;
+  // round half to even; a carry out of the mantissa raises the exponent, which is the rounded
+  // value (and infinity above the largest float)
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float((hw & 0x80000000u) | r);
+}
+
 // pair -> double: one FP64 addition.
 __device__ __forceinline__ double to_double(f32x2 x) { return widen(x.hi) + widen(x.lo); }
 
@@ -204,7 +228,14 @@ template <typename R, typename S>
 __device__ __forceinline__ R ldc(const S* p) { return Conv<R>::from(__ldg(p)); }
 
 __device__ __forceinline__ double to_dbl(double x) { return x; }
-__device__ __forceinline__ double to_dbl(float x) { return (double)x; }
+__device__ __forceinline__ double to_dbl(float x) { return dw::widen_exact(x); }
 __device__ __forceinline__ double to_dbl(f32x2 x) { return dw::to_double(x); }
+
+// A double stored in the element type T of an FP32 or FP64 result (integer rounding for FP32).
+template <typename T>
+__device__ __forceinline__ T store_as(double x) {
+  if constexpr (sizeof(T) == sizeof(float)) return dw::narrow(x);
+  else return x;
+}
 
 }  // namespace hzn

@@ -46,7 +46,24 @@ struct KParams {
   const double* geo_c;
   const double* geo_f;
   const double* geo_s;
+  // FP32 copies of the constants of the FP32 face arithmetic (filled by set_float_consts), so
+  // that the kernels load them instead of converting the doubles per face
+  float f_gamma, f_gfac, f_ch, f_ch2, f_idx, f_idy, f_idz, f_kappa, f_rho_floor, f_p_atm;
 };
+
+// Fill the FP32 copies of KParams' constants from the doubles (host side, once per context).
+inline void set_float_consts(KParams& kp) {
+  kp.f_gamma = (float)kp.gamma;
+  kp.f_gfac = (float)kp.gfac;
+  kp.f_ch = (float)kp.ch;
+  kp.f_ch2 = (float)(kp.ch * kp.ch);
+  kp.f_idx = (float)kp.idx;
+  kp.f_idy = (float)kp.idy;
+  kp.f_idz = (float)kp.idz;
+  kp.f_kappa = (float)kp.kappa;
+  kp.f_rho_floor = (float)kp.rho_floor;
+  kp.f_p_atm = (float)kp.p_atm;
+}
 
 constexpr int GEO_N = 10;  // alpha, 1/alpha, gamma_xx, _yy, _zz, gamma^xx, ^yy, ^zz, sqrt(gamma), sqrt(-g)
 constexpr int GEO_F = GEO_N + 1;  // face tables: GEO_N fields and alpha sqrt(gamma^dd)

@@ -79,11 +79,25 @@ __device__ __forceinline__ long long met_off(const KParams& kp, int i, int j, in
 template <typename R>
 __device__ __forceinline__ Consts<R> consts_of(const KParams& kp) {
   Consts<R> c;
-  c.gamma = cvt<R>(kp.gamma);
-  c.gfac = cvt<R>(kp.gfac);
-  c.ch = cvt<R>(kp.ch);
-  c.ch2 = cvt<R>(kp.ch * kp.ch);
+  if constexpr (SameType<R, float>::value) {
+    c.gamma = kp.f_gamma;
+    c.gfac = kp.f_gfac;
+    c.ch = kp.f_ch;
+    c.ch2 = kp.f_ch2;
+  } else {
+    c.gamma = cvt<R>(kp.gamma);
+    c.gfac = cvt<R>(kp.gfac);
+    c.ch = cvt<R>(kp.ch);
+    c.ch2 = cvt<R>(kp.ch * kp.ch);
+  }
   return c;
+}
+
+// A KParams constant in the face arithmetic's type: its FP32 copy for float.
+template <typename R>
+__device__ __forceinline__ R kconst(double d, float f) {
+  if constexpr (SameType<R, float>::value) return f;
+  else return cvt<R>(d);
 }
 
 // The ten metric values at one cell (only alpha and the diagonal for DIAG).
@@ -199,7 +213,7 @@ __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const
     const R sr = fmax(R(0), fmax(lpL, lpR));
     const R den = sr - sl;
     if (den != R(0)) {
-      const R iden = G.sqrtmg / den;
+      const R iden = fdiv(G.sqrtmg, den);
       wl = sr * iden;
       wr = -sl * iden;
       wu = sl * sr * iden;
@@ -209,7 +223,10 @@ __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const
     }
   }
 #pragma unroll
-  for (int f = 0; f < NV; ++f) out[f * ostride] = wl * FL[f] + (wr * FR[f] + wu * (UR[f] - UL[f]));
+  for (int f = 0; f < NV; ++f) {
+    if (CLEAN && (f == U_BX + D || f == U_PSI)) continue;  // the cleaning pair, below
+    out[f * ostride] = wl * FL[f] + (wr * FR[f] + wu * (UR[f] - UL[f]));
+  }
   if (CLEAN) {
     const int fb = U_BX + D;
     if constexpr (DIAG) {
@@ -227,6 +244,9 @@ __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const
         const R ic = G.sqrtmg / cden;
         out[fb * ostride] = (csr * FL[fb] - csl * FR[fb] + csl * csr * (UR[fb] - UL[fb])) * ic;
         out[U_PSI * ostride] = (csr * FL[U_PSI] - csl * FR[U_PSI] + csl * csr * (UR[U_PSI] - UL[U_PSI])) * ic;
+      } else {
+        out[fb * ostride] = wl * FL[fb] + (wr * FR[fb] + wu * (UR[fb] - UL[fb]));
+        out[U_PSI * ostride] = wl * FL[U_PSI] + (wr * FR[U_PSI] + wu * (UR[U_PSI] - UL[U_PSI]));
       }
     }
   }
@@ -288,7 +308,7 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
     if constexpr (!SameType<R, float>::value)
       cfac = ldc<R>(kp.geo_f + (D * GEO_F + GEO_N) * kp.ms + met_off(kp, i, j, k));
     else
-      cfac = G.alp * sqrt(sel<D>(G.ixx, G.iyy, G.izz));
+      cfac = G.alp * fsqrt(sel<D>(G.ixx, G.iyy, G.izz));
   }
   hlle_face<D, CLEAN, DIAG, false>(G, PL, PR, c, cfac, out, ostride);
 }
@@ -528,12 +548,12 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
       b2 = (G.gxx * bnx + 2.0 * (G.gxy * bny + G.gxz * bnz)) * bnx +
            (G.gyy * bny + 2.0 * G.gyz * bnz) * bny + G.gzz * bnz * bnz;
     }
-    P[P_BX] = (TP)(bnx * G.ialp);
-    P[P_BY] = (TP)(bny * G.ialp);
-    P[P_BZ] = (TP)(bnz * G.ialp);
-    P[P_PSI] = CLEAN ? (TP)(U[U_PSI] * isg) : TP(0);
-    P[P_RHO] = (TP)kp.rho_floor;
-    P[P_PRS] = (TP)kp.p_atm;
+    P[P_BX] = store_as<TP>(bnx * G.ialp);
+    P[P_BY] = store_as<TP>(bny * G.ialp);
+    P[P_BZ] = store_as<TP>(bnz * G.ialp);
+    P[P_PSI] = CLEAN ? store_as<TP>(U[U_PSI] * isg) : TP(0);
+    P[P_RHO] = kconst<TP>(kp.rho_floor, kp.f_rho_floor);
+    P[P_PRS] = kconst<TP>(kp.p_atm, kp.f_p_atm);
     P[P_UX] = P[P_UY] = P[P_UZ] = TP(0);
     // rest-mass plus internal energy density of the atmosphere: rho + p / (gamma - 1), with
     // 1 / (gamma - 1) = gamma / (gamma - 1) - 1
@@ -581,9 +601,11 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   const bool first_stage = sa.a0 == 0.0 && sa.ak == 1.0;  // U = Uk + dt L
   const Consts<R> c = consts_of<R>(kp);
   const Consts<double> cd = consts_of<double>(kp);
-  const R ridx = cvt<R>(kp.idx), ridy = cvt<R>(kp.idy), ridz = cvt<R>(kp.idz);
-  const R rhdx = cvt<R>(0.5 * kp.idx), rhdy = cvt<R>(0.5 * kp.idy), rhdz = cvt<R>(0.5 * kp.idz);
-  const R rkappa = cvt<R>(kp.kappa);
+  const R ridx = kconst<R>(kp.idx, kp.f_idx), ridy = kconst<R>(kp.idy, kp.f_idy);
+  const R ridz = kconst<R>(kp.idz, kp.f_idz);
+  const R rhdx = kconst<R>(0.5 * kp.idx, 0.5f * kp.f_idx), rhdy = kconst<R>(0.5 * kp.idy, 0.5f * kp.f_idy);
+  const R rhdz = kconst<R>(0.5 * kp.idz, 0.5f * kp.f_idz);
+  const R rkappa = kconst<R>(kp.kappa, kp.f_kappa);
   const S* __restrict__ P = (const S*)sa.Pin;
   S* __restrict__ Pout = (S*)sa.Pout;
 

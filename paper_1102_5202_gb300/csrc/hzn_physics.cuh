@@ -37,6 +37,17 @@ struct Consts {
   R ch2;    // cleaning speed squared
 };
 
+// Quotient and square root in the FP32 arithmetic of the mixed path's faces and of the
+// recovery's FP32 stage: the hardware approximations (__fdividef, within 2 ulps; x rsqrtf(x))
+// instead of the correctly rounded sequences, which that arithmetic's own rounding does not
+// need.  FP64 and double-word values keep the correctly rounded operations.
+template <typename R>
+__device__ __forceinline__ R fdiv(R a, R b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+template <typename R>
+__device__ __forceinline__ R fsqrt(R x) { return sqrt(x); }
+__device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 // 3+1 geometry at one point (face or centre), with the derived quantities the flux, speed and
 // source formulas need.  Built from the ten metric values alpha, beta^i, gamma_ij.
 template <typename R>
@@ -54,7 +65,7 @@ template <bool DIAG, typename R>
 __device__ __forceinline__ Geom<R> make_geom(const R m[10]) {
   Geom<R> G;
   G.alp = m[M_ALP];
-  G.ialp = R(1) / G.alp;
+  G.ialp = fdiv(R(1), G.alp);
   G.gxx = m[M_GXX];
   G.gyy = m[M_GYY];
   G.gzz = m[M_GZZ];
@@ -65,11 +76,11 @@ __device__ __forceinline__ Geom<R> make_geom(const R m[10]) {
     G.ixy = G.ixz = G.iyz = R(0);
     const R gyz2 = G.gyy * G.gzz;
     const R det = G.gxx * gyz2;
-    const R idet = R(1) / det;
+    const R idet = fdiv(R(1), det);
     G.ixx = gyz2 * idet;
     G.iyy = (G.gxx * G.gzz) * idet;
     G.izz = (G.gxx * G.gyy) * idet;
-    G.sqrtg = sqrt(det);
+    G.sqrtg = fsqrt(det);
     G.gtt = -G.alp * G.alp;
   } else {
     G.bx = m[M_BX];
@@ -82,14 +93,14 @@ __device__ __forceinline__ Geom<R> make_geom(const R m[10]) {
     const R cxy = G.gxz * G.gyz - G.gxy * G.gzz;
     const R cxz = G.gxy * G.gyz - G.gyy * G.gxz;
     const R det = G.gxx * cxx + G.gxy * cxy + G.gxz * cxz;
-    const R idet = R(1) / det;
+    const R idet = fdiv(R(1), det);
     G.ixx = cxx * idet;
     G.ixy = cxy * idet;
     G.ixz = cxz * idet;
     G.iyy = (G.gxx * G.gzz - G.gxz * G.gxz) * idet;
     G.iyz = (G.gxy * G.gxz - G.gxx * G.gyz) * idet;
     G.izz = (G.gxx * G.gyy - G.gxy * G.gxy) * idet;
-    G.sqrtg = sqrt(det);
+    G.sqrtg = fsqrt(det);
     G.blx = G.gxx * G.bx + G.gxy * G.by + G.gxz * G.bz;
     G.bly = G.gxy * G.bx + G.gyy * G.by + G.gyz * G.bz;
     G.blz = G.gxz * G.bx + G.gyz * G.by + G.gzz * G.bz;
@@ -154,7 +165,7 @@ __device__ __forceinline__ double rcp_fast(double x) {
   return 1.0 / x;
 #endif
 }
-__device__ __forceinline__ float rcp_fast(float x) { return 1.0f / x; }
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
 
 template <int D, typename R>
 __device__ __forceinline__ R sel(R x, R y, R z) {
@@ -347,7 +358,7 @@ __device__ __forceinline__ R cms2_of(const State<R>& S, const Consts<R>& c) {
   const R gp = c.gamma * S.p;
   const R wt = S.w + S.b2;
   if constexpr (FAST) return (gp * wt + S.b2 * (S.w - gp)) * rcp_fast(S.w * wt);
-  else return (gp * wt + S.b2 * (S.w - gp)) / (S.w * wt);
+  else return fdiv(gp * wt + S.b2 * (S.w - gp), S.w * wt);
 }
 
 // Characteristic speeds along D: roots of A l^2 + B l + C = 0 from the dispersion relation
@@ -378,8 +389,8 @@ __device__ __forceinline__ void speeds_of(const Geom<R>& G, const State<R>& S, R
     sq = disc > R(0) ? disc * rsqrt(disc) : R(0);
     i2a = R(0.5) * rcp_fast(A);
   } else {
-    sq = sqrt(disc);
-    i2a = R(0.5) / A;
+    sq = fsqrt(disc);
+    i2a = fdiv(R(0.5), A);
   }
   lp = (-B + sq) * i2a;
   lm = (-B - sq) * i2a;
@@ -421,7 +432,7 @@ __device__ __forceinline__ void speed_quadratic(const Geom<R>& G, const State<R>
 // with zero shift.
 template <int D, bool DIAG, typename R>
 __device__ __forceinline__ void clean_speeds(const Geom<R>& G, R ch, R& lm, R& lp) {
-  const R a = ch * G.alp * sqrt(sel<D>(G.ixx, G.iyy, G.izz));
+  const R a = ch * G.alp * fsqrt(sel<D>(G.ixx, G.iyy, G.izz));
   if constexpr (DIAG) {
     lm = -a;
     lp = a;
@@ -429,7 +440,7 @@ __device__ __forceinline__ void clean_speeds(const Geom<R>& G, R ch, R& lm, R& l
     // roots of l^2 + beta^D l - a^2 = 0: the pair's fluxes are alpha gamma^DD Psi and
     // c_h^2 alpha sqrt(-g) B^D - beta^D Psi
     const R hb = R(0.5) * sel<D>(G.bx, G.by, G.bz);
-    const R r = sqrt(hb * hb + a * a);
+    const R r = fsqrt(hb * hb + a * a);
     lm = -hb - r;
     lp = -hb + r;
   }
@@ -560,7 +571,7 @@ __device__ __forceinline__ NewtonStep<R> c2p_newton(R z, R v2, R e, R s, R q, R 
   const R j12 = zb * zb;
   const R j21 = R(1) - g1 * (R(1) - v2) + q * iz2 * iz;
   const R j22 = g1 * (z - R(0.5) * rs) + R(0.5) * b;
-  const R idet = R(1) / (j11 * j22 - j12 * j21);
+  const R idet = fdiv(R(1), j11 * j22 - j12 * j21);
   NewtonStep<R> st;
   st.dz = -(j22 * r1 - j12 * r2) * idet;
   st.dv = -(j11 * r2 - j21 * r1) * idet;
@@ -632,8 +643,8 @@ static __device__ __noinline__ bool c2p_bracketed(const C2PScalars q, double zgu
 // multiplies the relative error by about the FP32 root's, 2^-24).  Four FP64 instructions and
 // two conversions instead of a correctly rounded FP64 square root.  a > 0, af > 0.
 __device__ __forceinline__ double sqrt_from_f32(double a, float af) {
-  const float s = sqrtf(af);
-  const double sd = (double)s, h = (double)(0.5f / s);
+  const float s = fsqrt(af);
+  const double sd = (double)s, h = (double)__fdividef(0.5f, s);
   double r = fma(fma(-sd, sd, a), h, sd);
   return fma(fma(-r, r, a), h, r);
 }
@@ -648,14 +659,14 @@ struct C2PJac32 {
 __device__ __forceinline__ C2PJac32 c2p_jac32(float zf, float vf, float bf, float qf, float gf) {
   const float omf = 1.0f - vf;
   const float rs = rsqrtf(omf);
-  const float iz = 1.0f / zf;
+  const float iz = __fdividef(1.0f, zf);
   const float iz2 = iz * iz;
   const float zbf = zf + bf;
   const float j11 = 2.0f * zbf * vf + 2.0f * qf * zbf * iz2 * iz;
   const float j12 = zbf * zbf;
   const float j21 = 1.0f - gf * omf + qf * iz2 * iz;
   const float j22 = gf * (zf - 0.5f * rs) + 0.5f * bf;
-  const float idet = 1.0f / (j11 * j22 - j12 * j21);
+  const float idet = __fdividef(1.0f, j11 * j22 - j12 * j21);
   C2PJac32 J;
   J.a11 = j22 * idet;
   J.a12 = -j12 * idet;
@@ -884,20 +895,21 @@ __device__ __forceinline__ C2PResult con2prim(const Geom<double>& G, const doubl
     P[P_PSI] = CLEAN ? U[U_PSI] * isg : 0.0;
   } else {
     // result stored in FP32: everything but p from FP32 copies of the FP64 quantities
-    const TP rWf = ONE_FINISH ? (TP)sqrtf(om_seed) : (TP)rW, Zf = (TP)Z, ia = (TP)G.ialp;
-    const TP Bxf = (TP)Bx, Byf = (TP)By, Bzf = (TP)Bz;
-    const TP W = TP(1) / rWf;
-    const TP iZB = TP(1) / (Zf + (TP)B2);
-    const TP sbz = (TP)SB / Zf;
-    P[P_RHO] = (TP)Dd * rWf;
-    P[P_PRS] = (TP)p;
-    P[P_UX] = W * ((TP)Sux + sbz * Bxf) * iZB;
-    P[P_UY] = W * ((TP)Suy + sbz * Byf) * iZB;
-    P[P_UZ] = W * ((TP)Suz + sbz * Bzf) * iZB;
+    const TP rWf = ONE_FINISH ? fsqrt(om_seed) : store_as<TP>(rW);
+    const TP Zf = store_as<TP>(Z), ia = store_as<TP>(G.ialp);
+    const TP Bxf = store_as<TP>(Bx), Byf = store_as<TP>(By), Bzf = store_as<TP>(Bz);
+    const TP W = fdiv(TP(1), rWf);
+    const TP iZB = fdiv(TP(1), Zf + store_as<TP>(B2));
+    const TP sbz = fdiv(store_as<TP>(SB), Zf);
+    P[P_RHO] = store_as<TP>(Dd) * rWf;
+    P[P_PRS] = store_as<TP>(p);
+    P[P_UX] = W * (store_as<TP>(Sux) + sbz * Bxf) * iZB;
+    P[P_UY] = W * (store_as<TP>(Suy) + sbz * Byf) * iZB;
+    P[P_UZ] = W * (store_as<TP>(Suz) + sbz * Bzf) * iZB;
     P[P_BX] = Bxf * ia;
     P[P_BY] = Byf * ia;
     P[P_BZ] = Bzf * ia;
-    P[P_PSI] = CLEAN ? (TP)(U[U_PSI] * isg) : TP(0);
+    P[P_PSI] = CLEAN ? store_as<TP>(U[U_PSI] * isg) : TP(0);
   }
   res.ok = 1;
   return res;

@@ -18,6 +18,7 @@ inline float __fsub_rn(float a, float b) { return a - b; }
 inline float __fmul_rn(float a, float b) { return a * b; }
 inline float __fmaf_rn(float a, float b, float c) { return std::fma(a, b, c); }
 inline float __frcp_rn(float a) { return 1.0f / a; }
+inline float __fdividef(float a, float b) { return a / b; }
 inline float rsqrtf(float a) { return 1.0f / std::sqrt(a); }
 inline double rsqrt(double a) { return 1.0 / std::sqrt(a); }
 inline float rsqrt(float a) { return 1.0f / std::sqrt(a); }

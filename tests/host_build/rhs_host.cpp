@@ -52,6 +52,7 @@ void setup(Host& h, const int n[3], const double dx[3], const int bc[3], double 
   kp.gfac = gamma / (gamma - 1.0);
   kp.ch = clean ? ch : 0.0;
   kp.kappa = clean ? kappa : 0.0;
+  set_float_consts(kp);
 
   h.P.assign((size_t)(9 * kp.fs), nan);
   for (int f = 0; f < 9; ++f)
@@ -264,6 +265,7 @@ extern "C" void dev_recover(long n, double gamma, int clean, int diag, double rh
   kp.c2p_maxit = maxit;
   kp.c2p_tol = tol;
   kp.c2p_step_tol = 0.01 * std::sqrt(tol);
+  set_float_consts(kp);
   const Consts<double> c = consts_of<double>(kp);
   for (long q = 0; q < n; ++q) {
     double* U = cons + 9 * q;
