@@ -116,6 +116,138 @@ __device__ __forceinline__ void load_metric(const KParams& kp, const S* __restri
   }
 }
 
+// The HLLE weights of an FP64 face from its two states' speed quadratics (speed_quadratic: the
+// roots are (-b -+ sq) / A' with A' > 0).  The bounds sL = min(0, lambda-), sR = max(0,
+// lambda+) are chosen by cross-multiplied comparisons and kept as fractions n / d (n = 0, d = 1
+// for a bound clamped at 0); then wL = nR dL / Q, wR = -nL dR / Q and wU = nL nR / Q with
+// Q = nR dL - nL dR, so one reciprocal serves the face.  The weights carry sqrt(-g) (the flux
+// and conserved vectors are formed without it).
+__device__ __forceinline__ void hlle_weights(double sqrtmg, double AL, double BL, double sqL, double AR,
+                                             double BR, double sqR, double& wl, double& wr, double& wu) {
+  const double nmL = -BL - sqL, nmR = -BR - sqR, npL = -BL + sqL, npR = -BR + sqR;
+  const double dL = AL, dR = AR;
+  const bool lowL = nmL * dR < nmR * dL;
+  double nl = lowL ? nmL : nmR, dl = lowL ? dL : dR;
+  if (!(nl < 0.0)) {
+    nl = 0.0;
+    dl = 1.0;
+  }
+  const bool highL = npL * dR > npR * dL;
+  double nr = highL ? npL : npR, dr = highL ? dL : dR;
+  if (!(nr > 0.0)) {
+    nr = 0.0;
+    dr = 1.0;
+  }
+  const double q = nr * dl - nl * dr;
+  if (q != 0.0) {
+    const double iq = sqrtmg * rcp_fast(q);
+    wl = nr * dl * iq;
+    wr = -nl * dr * iq;
+    wu = nl * nr * iq;
+  } else {
+    wl = wr = 0.5 * sqrtmg;
+    wu = 0.0;
+  }
+}
+
+// One state's share of an FP64 HLLE face flux, added to acc: cf F + cu U with F the state's
+// flux vector along D and U its conserved vector (both divided by sqrt(-g), §2.1 Eq. 2), the
+// cleaning pair (B^D, Psi) excluded when cleaning is on.  HLLE is linear in F_L, F_R and
+// U_R - U_L, so (cf, cu) = (wL, -wU) for the left state and (wR, wU) for the right; F and U
+// are never formed: with k = cf u^D + cu u^t, m = (w + b^2) k and n = cf b^D + cu b^t,
+//   D:   rho k
+//   T_t: m u_t - n b_t + cu (p + b^2/2)
+//   T_i: m u_i - n b_i + cf (p + b^2/2) delta_iD
+//   B^j: cf (B^j u^D - B^D u^j) / u^t + cu B^j            (B^D: cu B^D without cleaning)
+// and, on a general metric with cleaning, cf psi gamma^{Dj} on B^j (j != D).
+template <int D, bool CLEAN, bool DIAG, bool FIRST>
+__device__ __forceinline__ void hlle_share(const Geom<double>& G, const State<double>& S, double cf,
+                                           double cu, double acc[9]) {
+  const double ud = sel<D>(S.ux, S.uy, S.uz);
+  const double bd = sel<D>(S.bx, S.by, S.bz);
+  const double Bd = sel<D>(S.Bx, S.By, S.Bz);
+  const double wt = S.w + S.b2, pt = S.p + 0.5 * S.b2;
+  const double k = cf * ud + cu * S.ut;
+  const double m = wt * k;
+  const double n = cf * bd + cu * S.bt;
+  const double cfi = cf * S.iut;
+  double v[9];
+  v[U_D] = S.rho * k;
+  v[U_TT] = m * S.l_t - n * S.b_t + cu * pt;
+  v[U_TX] = m * S.lx - n * S.b_x + (D == 0 ? cf * pt : 0.0);
+  v[U_TY] = m * S.ly - n * S.b_y + (D == 1 ? cf * pt : 0.0);
+  v[U_TZ] = m * S.lz - n * S.b_z + (D == 2 ? cf * pt : 0.0);
+  v[U_BX] = D == 0 ? cu * S.Bx : cfi * (S.Bx * ud - Bd * S.ux) + cu * S.Bx;
+  v[U_BY] = D == 1 ? cu * S.By : cfi * (S.By * ud - Bd * S.uy) + cu * S.By;
+  v[U_BZ] = D == 2 ? cu * S.Bz : cfi * (S.Bz * ud - Bd * S.uz) + cu * S.Bz;
+  if constexpr (CLEAN && !DIAG) {
+    const double cp = cf * S.psi;
+    if (D != 0) v[U_BX] += cp * sel<D>(G.ixx, G.ixy, G.ixz);
+    if (D != 1) v[U_BY] += cp * sel<D>(G.ixy, G.iyy, G.iyz);
+    if (D != 2) v[U_BZ] += cp * sel<D>(G.ixz, G.iyz, G.izz);
+  }
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (CLEAN && f == U_BX + D) continue;  // the cleaning pair has its own bounds
+    acc[f] = FIRST ? v[f] : acc[f] + v[f];
+  }
+}
+
+// HLLE flux (§2.2) of an FP64 face, written to out[f * ostride]: both states' speeds, the HLLE
+// weights (hlle_weights), then each state's share (hlle_share).  The cleaning pair (B^D, Psi)
+// takes HLLE at its own bounds; its flux and conserved components (divided by sqrt(-g)) are
+// F_BD = psi gamma^DD, U_BD = B^D, F_Psi = (c_h^2 alpha^2 B^D - beta^D psi) / alpha and
+// U_Psi = psi / alpha.  cfac: alpha sqrt(gamma^DD) at the face (DIAG with cleaning).
+template <int D, bool CLEAN, bool DIAG>
+__device__ __forceinline__ void hlle_face_fp64(const Geom<double>& G, const double PL[9],
+                                               const double PR[9], const Consts<double>& c,
+                                               double cfac, double* out, int ostride) {
+  const State<double> SL = make_state<DIAG>(G, PL, c);
+  const State<double> SR = make_state<DIAG>(G, PR, c);
+  double AL, BL, sqL, AR, BR, sqR;
+  speed_quadratic<D, DIAG>(G, SL, c, AL, BL, sqL);
+  speed_quadratic<D, DIAG>(G, SR, c, AR, BR, sqR);
+  double wl, wr, wu;
+  hlle_weights(G.sqrtmg, AL, BL, sqL, AR, BR, sqR, wl, wr, wu);
+  double acc[9];
+  hlle_share<D, CLEAN, DIAG, true>(G, SL, wl, -wu, acc);
+  hlle_share<D, CLEAN, DIAG, false>(G, SR, wr, wu, acc);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) {
+    if (CLEAN && f == U_BX + D) continue;
+    out[f * ostride] = acc[f];
+  }
+  if (CLEAN) {
+    const int fb = U_BX + D;
+    const double BdL = sel<D>(SL.Bx, SL.By, SL.Bz), BdR = sel<D>(SR.Bx, SR.By, SR.Bz);
+    const double gdd = sel<D>(G.ixx, G.iyy, G.izz);
+    if constexpr (DIAG) {
+      // zero shift: bounds -+a, a = c_h alpha sqrt(gamma^DD): weights sqrt(-g)/2 per state and
+      // a sqrt(-g)/2 for the jump
+      const double hs = 0.5 * G.sqrtmg, ha = hs * (c.ch * cfac);
+      out[fb * ostride] = hs * (gdd * (SL.psi + SR.psi)) - ha * (BdR - BdL);
+      out[U_PSI * ostride] = hs * (c.ch2 * G.alp * (BdL + BdR)) - ha * (G.ialp * (SR.psi - SL.psi));
+    } else {
+      const double bD = sel<D>(G.bx, G.by, G.bz);
+      const double FbL = SL.psi * gdd, FbR = SR.psi * gdd;
+      const double FpL = G.ialp * (c.ch2 * G.alp * G.alp * BdL - bD * SL.psi);
+      const double FpR = G.ialp * (c.ch2 * G.alp * G.alp * BdR - bD * SR.psi);
+      double cm, cp;
+      clean_speeds<D, DIAG>(G, c.ch, cm, cp);
+      const double csl = fmin(0.0, cm), csr = fmax(0.0, cp);
+      const double cden = csr - csl;
+      if (cden != 0.0) {
+        const double ic = G.sqrtmg / cden;
+        out[fb * ostride] = (csr * FbL - csl * FbR + csl * csr * (BdR - BdL)) * ic;
+        out[U_PSI * ostride] = (csr * FpL - csl * FpR + csl * csr * (G.ialp * (SR.psi - SL.psi))) * ic;
+      } else {
+        out[fb * ostride] = wl * FbL + (wr * FbR + wu * (BdR - BdL));
+        out[U_PSI * ostride] = wl * FpL + (wr * FpR + wu * (G.ialp * (SR.psi - SL.psi)));
+      }
+    }
+  }
+}
+
 // HLLE flux (§2.2) of one face from its reconstructed left / right primitive states and face
 // geometry, written to out[f * ostride].  ROLL: one copy of the state code serves both states
 // (a loop the compiler keeps rolled), which halves the code of the double-word path.  cfac:
@@ -310,7 +442,8 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
     else
       cfac = G.alp * fsqrt(sel<D>(G.ixx, G.iyy, G.izz));
   }
-  hlle_face<D, CLEAN, DIAG, false>(G, PL, PR, c, cfac, out, ostride);
+  if constexpr (SameType<R, double>::value) hlle_face_fp64<D, CLEAN, DIAG>(G, PL, PR, c, cfac, out, ostride);
+  else hlle_face<D, CLEAN, DIAG, false>(G, PL, PR, c, cfac, out, ostride);
 }
 
 // One face of the double-word path with its direction D given at run time (one copy of the
