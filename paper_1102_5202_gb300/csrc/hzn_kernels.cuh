@@ -388,15 +388,24 @@ __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const
 // HLLE flux of the face at i - 1/2 along D of cell (i, j, k) (the face between cells i-1 and
 // i along D), written to out[f * ostride].
 // RECON 0: TVD with the MC limiter (stencil c-2 .. c+1); 1: PPM (stencil c-3 .. c+2).
-template <int D, bool CLEAN, bool DIAG, int RECON, typename R, typename S>
+// ZC (z faces, MC reconstruction): 0 plain; 1 the z-march's first face, which also leaves in zc
+// the carry of the next face up; 2 a face whose left state and lower half-stencil come from that
+// carry (and which leaves the next one).  For the face k - 1/2 (cells k - 2 .. k + 1) the carry
+// is, per field, P_k + sigma_k (the next face's left state), P_{k+1} and P_{k+1} - P_k, so the
+// next face needs one load, one difference, one limited slope and two face values: the same
+// operations on the same operands as the plain stencil, three FP64 operations and three loads
+// fewer per field.  zc: this thread's carry, value q of field f at zc[(3 f + q) zs].
+template <int D, bool CLEAN, bool DIAG, int RECON, int ZC = 0, typename R, typename S>
 __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict__ P,
                                           const S* __restrict__ M, int i, int j, int k, R* out,
-                                          int ostride) {
+                                          int ostride, R* zc = nullptr, int zs = 0) {
+  static_assert(ZC == 0 || (D == 2 && RECON == 0), "the carry serves MC z faces");
   constexpr int NV = CLEAN ? 9 : 8;
   constexpr int NS = RECON ? 6 : 4;
   long long off[NS];  // stencil cells s = -NS/2 .. NS/2 - 1 along D
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
+    if (ZC == 2 && s < NS - 1) continue;  // only the top cell is new
     int ii = i, jj = j, kk = k;
     if (D == 0) ii = bc_index(i + s - NS / 2, kp.nx, kp.bcx);
     if (D == 1) jj = bc_index(j + s - NS / 2, kp.ny, kp.bcy);
@@ -407,12 +416,30 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
 #pragma unroll
   for (int f = 0; f < NV; ++f) {
     const S* pf = P + f * kp.fs;
-    if constexpr (RECON == 0) {
+    if constexpr (ZC == 2) {
+      R* cf = zc + 3 * f * zs;
+      const R cc = cf[zs], d1 = cf[2 * zs];
+      const R d = ldc<R>(pf + off[3]);
+      const R d2 = d - cc;
+      const R h = mc_half_slope(d1, d2);
+      PL[f] = cf[0];
+      PR[f] = cc - h;
+      cf[0] = cc + h;
+      cf[zs] = d;
+      cf[2 * zs] = d2;
+    } else if constexpr (RECON == 0) {
       const R a = ldc<R>(pf + off[0]), b = ldc<R>(pf + off[1]);
       const R cc = ldc<R>(pf + off[2]), d = ldc<R>(pf + off[3]);
       const R d0 = b - a, d1 = cc - b, d2 = d - cc;
       PL[f] = b + mc_half_slope(d0, d1);
-      PR[f] = cc - mc_half_slope(d1, d2);
+      const R h = mc_half_slope(d1, d2);
+      PR[f] = cc - h;
+      if constexpr (ZC == 1) {
+        R* cf = zc + 3 * f * zs;
+        cf[0] = cc + h;
+        cf[zs] = d;
+        cf[2 * zs] = d2;
+      }
     } else {
       ppm_face<R>(ldc<R>(pf + off[0]), ldc<R>(pf + off[1]), ldc<R>(pf + off[2]),
                   ldc<R>(pf + off[3]), ldc<R>(pf + off[4]), ldc<R>(pf + off[5]), PL[f], PR[f]);
@@ -723,6 +750,11 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   __shared__ R fx[NV][TY][TX + 1];
   __shared__ R fy[YA ? NV : 1][YA ? TY + 1 : 1][TX];
   __shared__ R fz[ZA ? 2 : 1][ZA ? NV : 1][TY][TX];
+  // z-face reconstruction carry (face_flux ZC), three values per field and thread, in dynamic
+  // shared memory (it does not fit the 48 KB of static shared memory beside the face fluxes)
+  constexpr bool ZCARRY = ZA && !PAIR && RECON == 0;
+  extern __shared__ __align__(16) unsigned char hz_dyn_smem[];
+  R* const zc = reinterpret_cast<R*>(hz_dyn_smem) + threadIdx.x;
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -746,7 +778,12 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   int nfail = 0, maxit = 0;
 
   if constexpr (!PAIR) {
-    if (ZA && own) face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX);
+    if (ZA && own) {
+      if constexpr (ZCARRY)
+        face_flux<2, CLEAN, DIAG, RECON, 1>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX, zc, NT);
+      else
+        face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX);
+    }
   }
 
   for (int k = kz0; k < kz1; ++k) {
@@ -808,7 +845,12 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
     } else {
     if (i <= kp.nx && j < kp.ny) face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, i, j, k, &fx[0][ty][tx], TY * (TX + 1));
     if (YA && i < kp.nx && j <= kp.ny) face_flux<1, CLEAN, DIAG, RECON>(kp, P, M, i, j, k, &fy[0][ty][tx], (TY + 1) * TX);
-    if (ZA && own) face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
+    if (ZA && own) {
+      if constexpr (ZCARRY)
+        face_flux<2, CLEAN, DIAG, RECON, 2>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX, zc, NT);
+      else
+        face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
+    }
     if (YA) {
       // top row of y-faces of the tile: warp 0; right column of x-faces: warp 1
       if (threadIdx.x < TX) {
@@ -1011,14 +1053,23 @@ void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, 
   constexpr int TX = 32;
   constexpr int TY = (!YA && !ZA) ? 1 : 4;
   using S = typename Prec<MIXED>::S;
+  using R = typename FaceType<PAIR, MIXED>::R;
   const S* M = (const S*)Mv;
   dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, zchunks);
+  // dynamic shared memory: the z-face reconstruction carry of the MC kernels (k_substep)
+  constexpr bool ZCARRY = ZA && !PAIR && RECON == 0;
+  const int nv = v.clean ? 9 : 8;
+  const size_t dyn = ZCARRY ? (size_t)3 * nv * TX * TY * sizeof(R) : 0;
+  auto go = [&](auto kern) {
+    if (dyn) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    kern<<<grid, TX * TY, dyn, st>>>(kp, sa, M, sc);
+  };
   if (v.clean) {
-    if (v.diag) k_substep<TX, TY, YA, ZA, true, true, MIXED, RECON, PAIR><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
-    else k_substep<TX, TY, YA, ZA, true, false, MIXED, RECON, PAIR><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    if (v.diag) go(k_substep<TX, TY, YA, ZA, true, true, MIXED, RECON, PAIR>);
+    else go(k_substep<TX, TY, YA, ZA, true, false, MIXED, RECON, PAIR>);
   } else {
-    if (v.diag) k_substep<TX, TY, YA, ZA, false, true, MIXED, RECON, PAIR><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
-    else k_substep<TX, TY, YA, ZA, false, false, MIXED, RECON, PAIR><<<grid, TX * TY, 0, st>>>(kp, sa, M, sc);
+    if (v.diag) go(k_substep<TX, TY, YA, ZA, false, true, MIXED, RECON, PAIR>);
+    else go(k_substep<TX, TY, YA, ZA, false, false, MIXED, RECON, PAIR>);
   }
 }
 
