@@ -160,28 +160,28 @@ __device__ __forceinline__ void hlle_weights(double sqrtmg, double AL, double BL
 //   T_i: m u_i - n b_i + cf (p + b^2/2) delta_iD
 //   B^j: cf (B^j u^D - B^D u^j) / u^t + cu B^j            (B^D: cu B^D without cleaning)
 // and, on a general metric with cleaning, cf psi gamma^{Dj} on B^j (j != D).
-template <int D, bool CLEAN, bool DIAG, bool FIRST>
-__device__ __forceinline__ void hlle_share(const Geom<double>& G, const State<double>& S, double cf,
-                                           double cu, double acc[9]) {
-  const double ud = sel<D>(S.ux, S.uy, S.uz);
-  const double bd = sel<D>(S.bx, S.by, S.bz);
-  const double Bd = sel<D>(S.Bx, S.By, S.Bz);
-  const double wt = S.w + S.b2, pt = S.p + 0.5 * S.b2;
-  const double k = cf * ud + cu * S.ut;
-  const double m = wt * k;
-  const double n = cf * bd + cu * S.bt;
-  const double cfi = cf * S.iut;
-  double v[9];
+template <int D, bool CLEAN, bool DIAG, bool FIRST, typename R>
+__device__ __forceinline__ void hlle_share(const Geom<R>& G, const State<R>& S, R cf, R cu,
+                                           R acc[9]) {
+  const R ud = sel<D>(S.ux, S.uy, S.uz);
+  const R bd = sel<D>(S.bx, S.by, S.bz);
+  const R Bd = sel<D>(S.Bx, S.By, S.Bz);
+  const R wt = S.w + S.b2, pt = S.p + R(0.5) * S.b2;
+  const R k = cf * ud + cu * S.ut;
+  const R m = wt * k;
+  const R n = cf * bd + cu * S.bt;
+  const R cfi = cf * S.iut;
+  R v[9];
   v[U_D] = S.rho * k;
   v[U_TT] = m * S.l_t - n * S.b_t + cu * pt;
-  v[U_TX] = m * S.lx - n * S.b_x + (D == 0 ? cf * pt : 0.0);
-  v[U_TY] = m * S.ly - n * S.b_y + (D == 1 ? cf * pt : 0.0);
-  v[U_TZ] = m * S.lz - n * S.b_z + (D == 2 ? cf * pt : 0.0);
+  v[U_TX] = m * S.lx - n * S.b_x + (D == 0 ? cf * pt : R(0));
+  v[U_TY] = m * S.ly - n * S.b_y + (D == 1 ? cf * pt : R(0));
+  v[U_TZ] = m * S.lz - n * S.b_z + (D == 2 ? cf * pt : R(0));
   v[U_BX] = D == 0 ? cu * S.Bx : cfi * (S.Bx * ud - Bd * S.ux) + cu * S.Bx;
   v[U_BY] = D == 1 ? cu * S.By : cfi * (S.By * ud - Bd * S.uy) + cu * S.By;
   v[U_BZ] = D == 2 ? cu * S.Bz : cfi * (S.Bz * ud - Bd * S.uz) + cu * S.Bz;
   if constexpr (CLEAN && !DIAG) {
-    const double cp = cf * S.psi;
+    const R cp = cf * S.psi;
     if (D != 0) v[U_BX] += cp * sel<D>(G.ixx, G.ixy, G.ixz);
     if (D != 1) v[U_BY] += cp * sel<D>(G.ixy, G.iyy, G.iyz);
     if (D != 2) v[U_BZ] += cp * sel<D>(G.ixz, G.iyz, G.izz);
@@ -193,24 +193,44 @@ __device__ __forceinline__ void hlle_share(const Geom<double>& G, const State<do
   }
 }
 
-// HLLE flux (§2.2) of an FP64 face, written to out[f * ostride]: both states' speeds, the HLLE
-// weights (hlle_weights), then each state's share (hlle_share).  The cleaning pair (B^D, Psi)
+// HLLE flux (§2.2) of an FP64 or FP32 face, written to out[f * ostride]: both states' speeds,
+// the HLLE weights, then each state's share (hlle_share).  FP64: the weights from the speed
+// quadratics as fractions (hlle_weights); FP32: from the plain roots per state (the
+// cross-multiplied comparisons of the fractions would leave the FP32 exponent range in
+// near-vacuum cells).  The cleaning pair (B^D, Psi)
 // takes HLLE at its own bounds; its flux and conserved components (divided by sqrt(-g)) are
 // F_BD = psi gamma^DD, U_BD = B^D, F_Psi = (c_h^2 alpha^2 B^D - beta^D psi) / alpha and
 // U_Psi = psi / alpha.  cfac: alpha sqrt(gamma^DD) at the face (DIAG with cleaning).
-template <int D, bool CLEAN, bool DIAG>
-__device__ __forceinline__ void hlle_face_fp64(const Geom<double>& G, const double PL[9],
-                                               const double PR[9], const Consts<double>& c,
-                                               double cfac, double* out, int ostride) {
-  const State<double> SL = make_state<DIAG>(G, PL, c);
-  const State<double> SR = make_state<DIAG>(G, PR, c);
-  double AL, BL, sqL, AR, BR, sqR;
-  speed_quadratic<D, DIAG>(G, SL, c, AL, BL, sqL);
-  speed_quadratic<D, DIAG>(G, SR, c, AR, BR, sqR);
-  double wl, wr, wu;
-  hlle_weights(G.sqrtmg, AL, BL, sqL, AR, BR, sqR, wl, wr, wu);
-  double acc[9];
-  hlle_share<D, CLEAN, DIAG, true>(G, SL, wl, -wu, acc);
+template <int D, bool CLEAN, bool DIAG, typename R>
+__device__ __forceinline__ void hlle_face_fused(const Geom<R>& G, const R PL[9], const R PR[9],
+                                                const Consts<R>& c, R cfac, R* out, int ostride) {
+  const State<R> SL = make_state<DIAG>(G, PL, c);
+  const State<R> SR = make_state<DIAG>(G, PR, c);
+  R wl, wr, wu;
+  if constexpr (SameType<R, double>::value) {
+    double AL, BL, sqL, AR, BR, sqR;
+    speed_quadratic<D, DIAG>(G, SL, c, AL, BL, sqL);
+    speed_quadratic<D, DIAG>(G, SR, c, AR, BR, sqR);
+    hlle_weights(G.sqrtmg, AL, BL, sqL, AR, BR, sqR, wl, wr, wu);
+  } else {
+    R lmL, lpL, lmR, lpR;
+    speeds_of<D, DIAG>(G, SL, cms2_of(SL, c), lmL, lpL);
+    speeds_of<D, DIAG>(G, SR, cms2_of(SR, c), lmR, lpR);
+    const R sl = fmin(R(0), fmin(lmL, lmR));
+    const R sr = fmax(R(0), fmax(lpL, lpR));
+    const R den = sr - sl;
+    if (den != R(0)) {
+      const R iden = fdiv(G.sqrtmg, den);
+      wl = sr * iden;
+      wr = -sl * iden;
+      wu = sl * sr * iden;
+    } else {
+      wl = wr = R(0.5) * G.sqrtmg;
+      wu = R(0);
+    }
+  }
+  R acc[9];
+  hlle_share<D, CLEAN, DIAG, true>(G, SL, wl, R(-wu), acc);
   hlle_share<D, CLEAN, DIAG, false>(G, SR, wr, wu, acc);
 #pragma unroll
   for (int f = 0; f < 8; ++f) {
@@ -219,25 +239,25 @@ __device__ __forceinline__ void hlle_face_fp64(const Geom<double>& G, const doub
   }
   if (CLEAN) {
     const int fb = U_BX + D;
-    const double BdL = sel<D>(SL.Bx, SL.By, SL.Bz), BdR = sel<D>(SR.Bx, SR.By, SR.Bz);
-    const double gdd = sel<D>(G.ixx, G.iyy, G.izz);
+    const R BdL = sel<D>(SL.Bx, SL.By, SL.Bz), BdR = sel<D>(SR.Bx, SR.By, SR.Bz);
+    const R gdd = sel<D>(G.ixx, G.iyy, G.izz);
     if constexpr (DIAG) {
       // zero shift: bounds -+a, a = c_h alpha sqrt(gamma^DD): weights sqrt(-g)/2 per state and
       // a sqrt(-g)/2 for the jump
-      const double hs = 0.5 * G.sqrtmg, ha = hs * (c.ch * cfac);
+      const R hs = R(0.5) * G.sqrtmg, ha = hs * (c.ch * cfac);
       out[fb * ostride] = hs * (gdd * (SL.psi + SR.psi)) - ha * (BdR - BdL);
       out[U_PSI * ostride] = hs * (c.ch2 * G.alp * (BdL + BdR)) - ha * (G.ialp * (SR.psi - SL.psi));
     } else {
-      const double bD = sel<D>(G.bx, G.by, G.bz);
-      const double FbL = SL.psi * gdd, FbR = SR.psi * gdd;
-      const double FpL = G.ialp * (c.ch2 * G.alp * G.alp * BdL - bD * SL.psi);
-      const double FpR = G.ialp * (c.ch2 * G.alp * G.alp * BdR - bD * SR.psi);
-      double cm, cp;
+      const R bD = sel<D>(G.bx, G.by, G.bz);
+      const R FbL = SL.psi * gdd, FbR = SR.psi * gdd;
+      const R FpL = G.ialp * (c.ch2 * G.alp * G.alp * BdL - bD * SL.psi);
+      const R FpR = G.ialp * (c.ch2 * G.alp * G.alp * BdR - bD * SR.psi);
+      R cm, cp;
       clean_speeds<D, DIAG>(G, c.ch, cm, cp);
-      const double csl = fmin(0.0, cm), csr = fmax(0.0, cp);
-      const double cden = csr - csl;
-      if (cden != 0.0) {
-        const double ic = G.sqrtmg / cden;
+      const R csl = fmin(R(0), cm), csr = fmax(R(0), cp);
+      const R cden = csr - csl;
+      if (cden != R(0)) {
+        const R ic = fdiv(G.sqrtmg, cden);
         out[fb * ostride] = (csr * FbL - csl * FbR + csl * csr * (BdR - BdL)) * ic;
         out[U_PSI * ostride] = (csr * FpL - csl * FpR + csl * csr * (G.ialp * (SR.psi - SL.psi))) * ic;
       } else {
@@ -469,8 +489,7 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
     else
       cfac = G.alp * fsqrt(sel<D>(G.ixx, G.iyy, G.izz));
   }
-  if constexpr (SameType<R, double>::value) hlle_face_fp64<D, CLEAN, DIAG>(G, PL, PR, c, cfac, out, ostride);
-  else hlle_face<D, CLEAN, DIAG, false>(G, PL, PR, c, cfac, out, ostride);
+  hlle_face_fused<D, CLEAN, DIAG>(G, PL, PR, c, cfac, out, ostride);
 }
 
 // One face of the double-word path with its direction D given at run time (one copy of the
