@@ -122,16 +122,16 @@ def test_stored_blob_counts_and_benchmark_constant():
 def test_benchmark_roofline_objects():
     """The roofline objects the benchmark prints, from a measured launch duration: the
     algorithmic rate is the op count per cell-substep times the cells over the duration, and
-    the kernel's executed figures sit beside it (captured 128^3 launch: 6.44 ms)."""
+    the kernel's executed figures sit beside it (captured 128^3 launch: 5.56 ms)."""
     import bench
-    cells, t = 128 ** 3, 6.44e-3
+    cells, t = 128 ** 3, 5.56e-3
     r = bench.fp64_roofline(cells, t)
     json.dumps(r)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(bench.FP64_ALG_FLOPS_PER_ZU / 3 * cells / t / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS)
-    assert 0.3 < r["frac"] < 0.4
-    assert 0.45 < r["implemented_fp64_flops"]["frac"] < 0.55  # 0.59 TFLOP/s in the capture
+    assert 0.35 < r["frac"] < 0.45
+    assert 0.43 < r["implemented_fp64_flops"]["frac"] < 0.53  # 0.58 TFLOP/s in the capture
     assert r["traffic"] == pytest.approx(bench.DRAM_BYTES_PER_CELL_SUBSTEP * cells)
     m = bench.mixed_roofline(cells, t / 8)
     json.dumps(m)
