@@ -275,6 +275,14 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   kp.c2p_1d = opts->c2p == HZ_C2P_1D;
   set_float_consts(kp);
   {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      kp.nsm = nsm;
+    else
+      kp.nsm = 1;
+  }
+  {
     const int ndims = kp.gx + kp.gy + kp.gz;
     kp.geo_c = geo;
     kp.geo_f = c->v.mixed ? nullptr : geo + GEO_N * L.ms;

@@ -34,7 +34,8 @@ struct KParams {
   double c2p_tol;
   double c2p_step_tol;   // Newton stops once a step is below this (0.01 sqrt(c2p_tol), relative)
   int c2p_1d;            // 1: the 1D recovery scheme (Newton in z, v^2 eliminated)
-  int zlen;              // cells of z per block
+  int zlen;              // cells of z per block (the chunked grid of the mixed and pair kernels)
+  int nsm;               // SMs of the device the context was created on
   // Geometry tables of a metric with zero shift and diagonal gamma (filled by hz_set_metric,
   // used by the DIAG kernels), in the metric's padded layout (field stride ms):
   //   geo_c  centre geometry, GEO_N fields (both precisions; FP64 values);

@@ -776,11 +776,6 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   R* const zc = reinterpret_cast<R*>(hz_dyn_smem) + threadIdx.x;
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int i = i0 + tx, j = j0 + ty;
-  const int kz0 = blockIdx.z * kp.zlen;
-  const int kz1 = min(kz0 + kp.zlen, kp.nz);
-  const bool own = i < kp.nx && j < kp.ny;
   const double dt = sc->dt;
   const bool first_stage = sa.a0 == 0.0 && sa.ak == 1.0;  // U = Uk + dt L
   const Consts<R> c = consts_of<R>(kp);
@@ -795,6 +790,35 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
 
   double vloc = 0.0;
   int nfail = 0, maxit = 0;
+
+  // FP64 kernels (bound by the FP64 pipe): a persistent grid; the plane-tiles (tile column, z)
+  // in column order are split into gridDim.x equal contiguous ranges, one per block, so that no
+  // partial last wave idles SMs; a range is one or more z segments of columns, each marched
+  // upwards from its first z face.  Mixed and double-word kernels (bound by latency): one block
+  // per tile column and z chunk (grid ntx x nty x chunks), whose launch order keeps the blocks
+  // running together on neighbouring tiles at the same heights, which share their halos in L2.
+  constexpr bool PERSIST = !MIXED && !PAIR;
+  const int ntx = (kp.nx + TX - 1) / TX, nty = (kp.ny + TY - 1) / TY;
+  const long long total = (long long)ntx * nty * kp.nz;
+  long long q = PERSIST ? total * blockIdx.x / gridDim.x : 0;
+  const long long q1 = PERSIST ? total * (blockIdx.x + 1) / gridDim.x : 1;
+  while (q < q1) {
+  long long col;
+  int kz0, kz1;
+  if constexpr (PERSIST) {
+    col = q / kp.nz;
+    kz0 = (int)(q - col * kp.nz);
+    kz1 = (int)min((long long)kp.nz, kz0 + (q1 - q));
+    q += kz1 - kz0;
+  } else {
+    col = (long long)blockIdx.y * ntx + blockIdx.x;
+    kz0 = blockIdx.z * kp.zlen;
+    kz1 = min(kz0 + kp.zlen, kp.nz);
+    q = q1;
+  }
+  const int i0 = (int)(col % ntx) * TX, j0 = (int)(col / ntx) * TY;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = i < kp.nx && j < kp.ny;
 
   if constexpr (!PAIR) {
     if (ZA && own) {
@@ -1001,6 +1025,7 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
     }
     __syncthreads();
   }
+  }  // z segments of this block
   block_stats<NT>(sc, vloc, nfail, maxit, sa.last != 0);
 }
 
@@ -1062,6 +1087,36 @@ inline int blocks_for(long long n, int threads) {
   return (int)b;
 }
 
+// One substep launch.  FP64 kernels run on a persistent grid: as many blocks as are resident at
+// once (blocks per SM from the occupancy calculator, once per instantiation, times the SMs),
+// each taking an equal share of the plane-tiles, but at least 8 plane-tiles per block.  Mixed
+// and double-word kernels: one block per tile column and z chunk.  dyn: the dynamic shared
+// memory (the z-face carry of the MC kernels).
+template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED, int RECON, bool PAIR>
+void launch_substep_one(const KParams& kp, const StageArgs& sa, const typename Prec<MIXED>::S* M,
+                        DevScalars* sc, size_t dyn, int zchunks, cudaStream_t st) {
+  auto kern = k_substep<TX, TY, YA, ZA, CLEAN, DIAG, MIXED, RECON, PAIR>;
+  static int per_sm = 0;  // one per instantiation
+  if (per_sm == 0) {
+    if (dyn) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TX * TY, dyn) != cudaSuccess || nb < 1)
+      nb = 1;
+    per_sm = nb;
+  }
+  if constexpr (MIXED || PAIR) {  // one block per tile column and z chunk (see k_substep)
+    const dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, zchunks);
+    kern<<<grid, TX * TY, dyn, st>>>(kp, sa, M, sc);
+    return;
+  }
+  const long long total = (long long)((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY) * kp.nz;
+  long long g = (long long)per_sm * (kp.nsm > 0 ? kp.nsm : 1);
+  const long long cap = (total + 7) / 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  kern<<<(unsigned)g, TX * TY, dyn, st>>>(kp, sa, M, sc);
+}
+
 // Launchers for one (precision, dimensionality); dispatch on cleaning and metric class.
 template <bool YA, bool ZA, bool MIXED, int RECON, bool PAIR = false>
 void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, const void* Mv,
@@ -1074,21 +1129,15 @@ void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, 
   using S = typename Prec<MIXED>::S;
   using R = typename FaceType<PAIR, MIXED>::R;
   const S* M = (const S*)Mv;
-  dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY, zchunks);
   // dynamic shared memory: the z-face reconstruction carry of the MC kernels (k_substep)
   constexpr bool ZCARRY = ZA && !PAIR && RECON == 0;
-  const int nv = v.clean ? 9 : 8;
-  const size_t dyn = ZCARRY ? (size_t)3 * nv * TX * TY * sizeof(R) : 0;
-  auto go = [&](auto kern) {
-    if (dyn) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    kern<<<grid, TX * TY, dyn, st>>>(kp, sa, M, sc);
-  };
+  const size_t dyn = ZCARRY ? (size_t)3 * (v.clean ? 9 : 8) * TX * TY * sizeof(R) : 0;
   if (v.clean) {
-    if (v.diag) go(k_substep<TX, TY, YA, ZA, true, true, MIXED, RECON, PAIR>);
-    else go(k_substep<TX, TY, YA, ZA, true, false, MIXED, RECON, PAIR>);
+    if (v.diag) launch_substep_one<TX, TY, YA, ZA, true, true, MIXED, RECON, PAIR>(kp, sa, M, sc, dyn, zchunks, st);
+    else launch_substep_one<TX, TY, YA, ZA, true, false, MIXED, RECON, PAIR>(kp, sa, M, sc, dyn, zchunks, st);
   } else {
-    if (v.diag) go(k_substep<TX, TY, YA, ZA, false, true, MIXED, RECON, PAIR>);
-    else go(k_substep<TX, TY, YA, ZA, false, false, MIXED, RECON, PAIR>);
+    if (v.diag) launch_substep_one<TX, TY, YA, ZA, false, true, MIXED, RECON, PAIR>(kp, sa, M, sc, dyn, zchunks, st);
+    else launch_substep_one<TX, TY, YA, ZA, false, false, MIXED, RECON, PAIR>(kp, sa, M, sc, dyn, zchunks, st);
   }
 }
 
