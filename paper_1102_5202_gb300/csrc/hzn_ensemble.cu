@@ -86,9 +86,10 @@ __device__ __forceinline__ void tube_face(const double* P, long long fs, int n, 
     PR[q] = cc - mc_half_slope(d1, d2);
   }
   PL[8] = PR[8] = 0.0;
-  // the grid kernel's HLLE of one face (FP64: both roots as fractions, one division)
+  // the grid kernel's HLLE of one face (FP64: both roots as fractions, one division; each
+  // state's weighted share added without forming its flux and conserved vectors)
   double F9[9];
-  hlle_face<0, false, true, false>(G, PL, PR, c, 0.0, F9, 1);
+  hlle_face_fused<0, false, true>(G, PL, PR, c, 0.0, F9, 1);
 #pragma unroll
   for (int q = 0; q < 8; ++q) F[q] = F9[q];
 }
@@ -101,7 +102,7 @@ __device__ __forceinline__ double cell_speed(const double* P, long long fs, int 
   Pc[8] = 0.0;
   const State<double> S = make_state<true>(G, Pc, c);
   double lm, lp;
-  speeds_of<0, true>(G, S, cms2_of(S, c), lm, lp);
+  speeds_of<0, true, double, true>(G, S, cms2_of<double, true>(S, c), lm, lp);
   return fmax(fabs(lm), fabs(lp)) * idx;
 }
 
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(NT, MINB) k_ensemble(const EnsParams ep) {
             if (stage == 2) {
               const State<double> S = make_state<true>(G, Pn, c);
               double lm, lp;
-              speeds_of<0, true>(G, S, cms2_of(S, c), lm, lp);
+              speeds_of<0, true, double, true>(G, S, cms2_of<double, true>(S, c), lm, lp);
               vloc = fmax(vloc, fmax(fabs(lm), fabs(lp)) * ti.idx);
             }
           }
