@@ -133,7 +133,7 @@ Layout layout_of(const hz_grid* g, const hz_options* o) {
   // geometry tables of a DIAG metric: centre geometry; in FP64 also face geometry and source
   // differences per active axis
   const int ndims = gx + gy + gz;
-  const int ngeo = o->precision == HZ_MIXED ? GEO_N : GEO_N + ndims * (GEO_F + GEO_S);
+  const int ngeo = o->precision == HZ_MIXED ? GEO_C : GEO_C + ndims * (GEO_F + GEO_S);
   L.geo = round_up((size_t)L.ms * ngeo * sizeof(double), 256);
   L.total = L.scal + L.met + 2 * L.u_bytes + 2 * L.p_bytes + L.geo;  // U0, U1, P[0], P[1], tables
   return L;
@@ -285,8 +285,8 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
   {
     const int ndims = kp.gx + kp.gy + kp.gz;
     kp.geo_c = geo;
-    kp.geo_f = c->v.mixed ? nullptr : geo + GEO_N * L.ms;
-    kp.geo_s = c->v.mixed ? nullptr : geo + GEO_N * L.ms + (long long)ndims * GEO_F * L.ms;
+    kp.geo_f = c->v.mixed ? nullptr : geo + GEO_C * L.ms;
+    kp.geo_s = c->v.mixed ? nullptr : geo + GEO_C * L.ms + (long long)ndims * GEO_F * L.ms;
   }
   // z chunks: enough blocks for several waves on 152 SMs
   int tx, ty;

@@ -38,7 +38,9 @@ struct KParams {
   int nsm;               // SMs of the device the context was created on
   // Geometry tables of a metric with zero shift and diagonal gamma (filled by hz_set_metric,
   // used by the DIAG kernels), in the metric's padded layout (field stride ms):
-  //   geo_c  centre geometry, GEO_N fields (both precisions; FP64 values);
+  //   geo_c  centre geometry, GEO_C fields (both precisions; FP64 values): the GEO_N fields
+  //          of Geom, then sum over active axes of alpha sqrt(gamma^dd) / dx_d (the CFL rate of a
+  //          state at rest per unit signal speed);
   //   geo_f  face geometry of axis d at geo_f + d GEO_F ms, the face i - 1/2 of cell (i, j, k)
   //          at the cell's metric offset: the GEO_N fields of the centre table, then
   //          alpha sqrt(gamma^dd) (the cleaning speed per unit c_h) (FP64 path only);
@@ -67,6 +69,7 @@ inline void set_float_consts(KParams& kp) {
 }
 
 constexpr int GEO_N = 10;  // alpha, 1/alpha, gamma_xx, _yy, _zz, gamma^xx, ^yy, ^zz, sqrt(gamma), sqrt(-g)
+constexpr int GEO_C = GEO_N + 1;  // centre table: GEO_N fields and sum_d alpha sqrt(gamma^dd) / dx_d
 constexpr int GEO_F = GEO_N + 1;  // face tables: GEO_N fields and alpha sqrt(gamma^dd)
 constexpr int GEO_S = 4;   // g_tt, g_xx, g_yy, g_zz
 

@@ -664,6 +664,21 @@ __device__ __forceinline__ double cell_max_speed(const KParams& kp, const Geom<R
   return v;
 }
 
+// The CFL rate of a cell just set to the atmosphere (u~ = 0) on a zero-shift diagonal metric, in
+// closed form: along every axis the dispersion relation has A = 1/alpha^2, B = 0 and
+// C = -c^2 gamma^dd, so lambda = -+ c alpha sqrt(gamma^dd), with c^2 = c_s^2 + v_A^2 - c_s^2 v_A^2
+// = (gamma p + b^2) / (w + b^2) for that state; with cleaning each axis's bound is
+// max(c, c_h) alpha sqrt(gamma^dd).  cfl_geo: sum_d alpha sqrt(gamma^dd) / dx_d (centre table).
+template <bool CLEAN>
+__device__ __forceinline__ double atm_cfl_rate(const KParams& kp, double b2, double cfl_geo) {
+  const double gp = kp.gamma * kp.p_atm;
+  const double w = fma(kp.gfac, kp.p_atm, kp.rho_floor);
+  const double c2 = (gp + b2) * rcp_fast(w + b2);
+  double c = c2 * rsqrt(c2);
+  if (CLEAN) c = fmax(c, kp.ch);
+  return c * cfl_geo;
+}
+
 #ifdef __CUDACC__  // device-only: block reduction, kernels, launchers (the helpers build for the host too)
 // Block reduction of the CFL maximum, the failure count and the largest iteration count.
 template <int NT>
@@ -701,10 +716,11 @@ __device__ __forceinline__ void block_stats(DevScalars* sc, double vloc, int nfa
 // Recovery with atmosphere / floor handling; rewrites U when the cell is reset.  TG, TP: the
 // element types of the guess and of the result (float for the mixed path, whose primitive
 // state is stored in FP32; a pressure-floor reset recomputes U from that stored state).
+// atm_b2: when not null and the cell is set to the atmosphere, receives that state's b^2.
 template <bool CLEAN, bool DIAG, bool ONE_FINISH = false, typename TG = double, typename TP = double>
 __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G, double U[9],
                                        const TG Pg[9], const Consts<double>& c, TP P[9],
-                                       int& iters) {
+                                       int& iters, double* atm_b2 = nullptr) {
   // atmosphere: a cell whose rest-mass density D / sqrt(gamma) = rho W is below rho_atm is not
   // recovered but set to the atmosphere state (the decision uses the conserved state only)
   const bool atm = U[U_D] < kp.rho_atm * G.sqrtg;
@@ -740,6 +756,7 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
     U[U_D] = G.sqrtg * kp.rho_floor;
     U[U_TT] = -G.sqrtmg * fma(0.5, b2, e_atm);
     U[U_TX] = U[U_TY] = U[U_TZ] = 0.0;
+    if (atm_b2) *atm_b2 = b2;
   } else if ((double)P[P_PRS] < kp.p_floor) {
     P[P_PRS] = (TP)kp.p_floor;
     double Pd[9];
@@ -999,8 +1016,14 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
 #pragma unroll
         for (int f = 0; f < NV; ++f) Pg[f] = __ldg(P + f * kp.fs + off);
         if (!CLEAN) Pg[8] = 0.0;
-        nfail += recover<CLEAN, DIAG>(kp, Gd, U, Pg, cd, Pn, it);
-        if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, Gd, Pn, cd));
+        double ab2 = -1.0;
+        nfail += recover<CLEAN, DIAG>(kp, Gd, U, Pg, cd, Pn, it, DIAG ? &ab2 : nullptr);
+        if (sa.last) {
+          if (DIAG && ab2 >= 0.0)
+            vloc = fmax(vloc, atm_cfl_rate<CLEAN>(kp, ab2, __ldg(kp.geo_c + GEO_N * kp.ms + mo)));
+          else
+            vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, Gd, Pn, cd));
+        }
       } else if constexpr (MIXED) {
         Geom<double> Gd;
         if constexpr (DIAG) {
@@ -1013,8 +1036,14 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         nfail += recover<CLEAN, DIAG, true, R, R>(kp, Gd, U, Pc, cd, Pn, it);
         if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pn, c));
       } else {
-        nfail += recover<CLEAN, DIAG>(kp, G, U, Pc, cd, Pn, it);
-        if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pn, c));
+        double ab2 = -1.0;
+        nfail += recover<CLEAN, DIAG>(kp, G, U, Pc, cd, Pn, it, DIAG ? &ab2 : nullptr);
+        if (sa.last) {
+          if (DIAG && ab2 >= 0.0)
+            vloc = fmax(vloc, atm_cfl_rate<CLEAN>(kp, ab2, __ldg(kp.geo_c + GEO_N * kp.ms + mo)));
+          else
+            vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pn, c));
+        }
       }
       maxit = max(maxit, it);
 #pragma unroll
@@ -1158,7 +1187,13 @@ __global__ void k_geo_tables(const KParams kp, const S* __restrict__ M, double* 
     if (cell) {
       double m[10];
       load_metric<true>(kp, M, mo, m);
-      geo_store(gc, mo, kp.ms, make_geom<true>(m));
+      const Geom<double> Gc = make_geom<true>(m);
+      geo_store(gc, mo, kp.ms, Gc);
+      // CFL rate of a state at rest per unit signal speed: sum_d alpha sqrt(gamma^dd) / dx_d
+      double r = Gc.alp * sqrt(Gc.ixx) * kp.idx;
+      if (ya) r += Gc.alp * sqrt(Gc.iyy) * kp.idy;
+      if (za) r += Gc.alp * sqrt(Gc.izz) * kp.idz;
+      gc[GEO_N * kp.ms + mo] = r;
     }
     if (!faces) continue;
 #pragma unroll

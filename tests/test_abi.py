@@ -45,10 +45,10 @@ def test_workspace_bytes_and_argument_checks(lib):
     o = hzn.make_options(2.0, cleaning=True, ch=0.5, kappa=1.0)
     nb = hzn.hz_workspace_bytes(g, o)
     # 10 padded metric fields + 4 state arrays of 9 padded fields + the geometry tables of a
-    # DIAG metric (centre 10 fields, faces 3 x 11, source differences 3 x 4; metric layout), FP64
+    # DIAG metric (centre 11 fields, faces 3 x 11, source differences 3 x 4; metric layout), FP64
     msize = 208 * 194 * 194
-    assert nb >= (10 * 194 ** 3 + 4 * 9 * 192 ** 3 + 55 * 194 ** 3) * 8
-    assert nb < (10 * msize + 4 * 9 * 192 ** 3 + 55 * msize + 4096) * 8
+    assert nb >= (10 * 194 ** 3 + 4 * 9 * 192 ** 3 + 56 * 194 ** 3) * 8
+    assert nb < (10 * msize + 4 * 9 * 192 ** 3 + 56 * msize + 4096) * 8
     bad = [
         (hzn.make_grid((1, 4, 4), (1, 1, 1), (0, 0, 0)), o, hzn.HZ_ERR_UNSUPPORTED),
         # degenerate grids: empty, negative, a single cell (no active axis)
