@@ -70,8 +70,8 @@ DRAM_BYTES_PER_CELL_SUBSTEP = 718.0
 # The same two figures for the mixed-precision substep kernel at 192^3
 # (profiles/k_substep_mixed_blob3d.md): FP64 flops (recovery, update) per cell per substep,
 # and DRAM bytes per cell per substep.
-MIXED_FP64_FLOPS_PER_CELL_SUBSTEP = 52.1
-MIXED_DRAM_BYTES_PER_CELL_SUBSTEP = 300.2
+MIXED_FP64_FLOPS_PER_CELL_SUBSTEP = 52.3
+MIXED_DRAM_BYTES_PER_CELL_SUBSTEP = 304.9
 # Algorithmic HBM bytes per zone update (three substeps, FP64, nine fields): read P, U_k, U0,
 # metric and write U_{k+1}, P_{k+1} once per substep; stage 1 reads U0 once.
 HBM_BYTES_PER_ZU = (46 + 55 + 55) * 8

@@ -162,6 +162,14 @@ const char* hz_strerror(int code);
 /* HZN_VERSION of the loaded library. */
 int hz_version(void);
 
+/* The CUDA runtime error code (a cudaError_t value) behind the last HZ_ERR_CUDA that a call of
+ * this library returned on the calling host thread; 0 if none has.  Not cleared by later calls
+ * that succeed.  No counterpart in the paper: it makes HZ_ERR_CUDA diagnosable. */
+int hz_last_cuda_error(void);
+
+/* Static description of a CUDA runtime error code (cudaGetErrorString). */
+const char* hz_cuda_error_string(int cuda_code);
+
 /* ---- Ensembles of independent 1-D tubes ------------------------------------------------
  * Many independent 1-D Riemann problems (the shock tubes of §5.1) advanced to a common end
  * time in one persistent launch.  Each tube has its own cell count n[t] >= 2, cell width dx[t]

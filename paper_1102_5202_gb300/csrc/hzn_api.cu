@@ -113,7 +113,15 @@ int grid_blocks(long long n, int threads) {
   return (int)b;
 }
 
-int cuda_err(cudaError_t e) { return e == cudaSuccess ? HZ_OK : HZ_ERR_CUDA; }
+static thread_local int t_last_cuda_error = 0;  // per host thread (hz_last_cuda_error)
+
+int record_cuda_error(cudaError_t e) {
+  if (e == cudaSuccess) return HZ_OK;
+  t_last_cuda_error = (int)e;
+  return HZ_ERR_CUDA;
+}
+
+int cuda_err(cudaError_t e) { return record_cuda_error(e); }
 
 Layout layout_of(const hz_grid* g, const hz_options* o) {
   Layout L;
@@ -281,6 +289,7 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
       kp.nsm = nsm;
     else
       kp.nsm = 1;
+    kp.dev = dev;
   }
   {
     const int ndims = kp.gx + kp.gy + kp.gz;
@@ -311,6 +320,10 @@ int ctx_init(hz_ctx* c, const hz_grid* grid, const hz_options* opts, void* d_wor
 extern "C" {
 
 int hz_version(void) { return HZN_VERSION; }
+
+int hz_last_cuda_error(void) { return t_last_cuda_error; }
+
+const char* hz_cuda_error_string(int cuda_code) { return cudaGetErrorString((cudaError_t)cuda_code); }
 
 const char* hz_strerror(int code) {
   switch (code) {
@@ -363,7 +376,7 @@ int hz_set_metric(hz_ctx* c, const double* d_metric) {
   const long long n = (long long)(c->g.n[0] + 2 * c->kp.gx) * (c->g.n[1] + 2 * c->kp.gy) *
                       (c->g.n[2] + 2 * c->kp.gz);
   cudaError_t e = cudaMemsetAsync(&c->sc->metric_general, 0, sizeof(unsigned int), c->st);
-  if (e != cudaSuccess) return HZ_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_err(e);
   if (c->v.mixed)
     k_pack_metric<float><<<grid_blocks(n * 10, 256), 256, 0, c->st>>>(c->kp, d_metric, (float*)c->met, c->sc);
   else
@@ -373,12 +386,12 @@ int hz_set_metric(hz_ctx* c, const double* d_metric) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&general, &c->sc->metric_general, sizeof(general), cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-  if (e != cudaSuccess) return HZ_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_err(e);
   c->v.diag = general ? 0 : 1;
   if (c->v.diag) {
     launch_geo_tables(c->v, c->kp, c->met, (double*)c->kp.geo_c, (double*)c->kp.geo_f,
                       (double*)c->kp.geo_s, c->st);
-    if (cudaGetLastError() != cudaSuccess) return HZ_ERR_CUDA;
+    if (const cudaError_t le = cudaGetLastError(); le != cudaSuccess) return cuda_err(le);
   }
   c->have_metric = 1;
   return HZ_OK;
@@ -394,7 +407,7 @@ int hz_set_primitives(hz_ctx* c, const double* d_prim) {
   // the second primitive buffer and U1 start as copies so that inactive fields stay defined
   cudaError_t e = cudaMemcpyAsync(c->P[1], c->P[0], L.p_bytes, cudaMemcpyDeviceToDevice, c->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->U1, c->U0, L.u_bytes, cudaMemcpyDeviceToDevice, c->st);
-  if (e != cudaSuccess) return HZ_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_err(e);
   k_reset_scalars<<<1, 1, 0, c->st>>>(c->sc);
   launch_max_speed(c->v, c->kp, c->P[0], c->met, c->sc, c->st);
   c->have_prim = 1;
@@ -433,7 +446,7 @@ int hz_max_speed(hz_ctx* c, double* h_out) {
   unsigned long long bits = 0;
   cudaError_t e = cudaMemcpyAsync(&bits, &c->sc->vmax_bits, sizeof(bits), cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-  if (e != cudaSuccess) return HZ_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_err(e);
   double v;
   memcpy(&v, &bits, sizeof(v));
   *h_out = v;
@@ -445,7 +458,7 @@ int hz_get_stats(hz_ctx* c, hz_stats* h_out) {
   DevScalars s;
   cudaError_t e = cudaMemcpyAsync(&s, c->sc, sizeof(s), cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-  if (e != cudaSuccess) return HZ_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_err(e);
   h_out->c2p_failures = (long long)s.fails;
   h_out->c2p_max_iters = s.maxit;
   double v;
@@ -478,12 +491,14 @@ void* g_noalloc_addr[kNoallocMaxDevices];  // device address of g_noalloc_scratc
 // Device address of the scratch array on the current device (looked up on first use).
 int noalloc_scratch(void** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HZ_ERR_CUDA;
+  if (const cudaError_t e = cudaGetDevice(&dev); e != cudaSuccess) return cuda_err(e);
   if (dev < 0 || dev >= kNoallocMaxDevices) return HZ_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HZ_ERR_CUDA;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (!p) return HZ_ERR_CUDA;
     g_noalloc_addr[dev] = p;
   }
   *out = g_noalloc_addr[dev];
@@ -517,6 +532,6 @@ extern "C" int hz_step_noalloc(const hz_grid* grid, const hz_options* opts, cons
   unsigned long long fails = 0;
   cudaError_t ce = cudaMemcpyAsync(&fails, &c.sc->fails, sizeof(fails), cudaMemcpyDeviceToHost, c.st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c.st);
-  if (ce != cudaSuccess) return HZ_ERR_CUDA;
+  if (ce != cudaSuccess) return cuda_err(ce);
   return fails ? HZ_WARN_C2P : HZ_OK;
 }

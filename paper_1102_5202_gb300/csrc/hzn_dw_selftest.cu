@@ -51,7 +51,7 @@ extern "C" int hz_rcp_selftest(const double* d_x, double* d_out, long long n, vo
   if (!d_x || !d_out || n < 0) return HZ_ERR_ARG;
   if (n == 0) return HZ_OK;
   k_rcp_selftest<<<blocks_of(n, 256), 256, 0, (cudaStream_t)stream>>>(d_x, d_out, n);
-  return cudaGetLastError() == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+  return hzn::record_cuda_error(cudaGetLastError());
 }
 
 extern "C" int hz_dw_selftest(const double* d_a, const double* d_b, double* d_out, long long n,
@@ -62,5 +62,5 @@ extern "C" int hz_dw_selftest(const double* d_a, const double* d_b, double* d_ou
   const long long want = (n + threads - 1) / threads;
   const int blocks = (int)(want < 4096 ? want : 4096);
   k_dw_selftest<<<blocks, threads, 0, (cudaStream_t)stream>>>(d_a, d_b, d_out, n);
-  return cudaGetLastError() == cudaSuccess ? HZ_OK : HZ_ERR_CUDA;
+  return hzn::record_cuda_error(cudaGetLastError());
 }

@@ -343,7 +343,7 @@ EnsLayout ens_layout(int ntubes, const int* n) {
   return L;
 }
 
-int cuda_err(cudaError_t e) { return e == cudaSuccess ? HZ_OK : HZ_ERR_CUDA; }
+int cuda_err(cudaError_t e) { return record_cuda_error(e); }
 
 }  // namespace
 
@@ -374,7 +374,7 @@ int ens_launch(hz_ensemble* e, double t_end, double cfl, long long max_steps) {
   e->ep.cfl = cfl;
   e->ep.max_steps = max_steps;
   cudaError_t err = cudaMemsetAsync(e->ep.queue, 0, sizeof(int), e->st);
-  if (err != cudaSuccess) return HZ_ERR_CUDA;
+  if (err != cudaSuccess) return cuda_err(err);
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -501,7 +501,7 @@ int hz_ensemble_create(hz_ensemble** out, int ntubes, const int* h_n, const doub
   if (err == cudaSuccess) err = cudaMemset(d_res, 0, sizeof(TubeResult) * ntubes);
   if (err != cudaSuccess) {
     delete e;
-    return HZ_ERR_CUDA;
+    return cuda_err(err);
   }
   *out = e;
   return HZ_OK;
@@ -518,7 +518,7 @@ int hz_ensemble_set_primitives(hz_ensemble* e, const double* d_prim) {
   const long long total = e->L.npad;
   // zero the state (padding cells stay defined), then scatter the tubes
   cudaError_t err = cudaMemsetAsync(e->ep.U0, 0, 4 * e->L.state_b, e->st);
-  if (err != cudaSuccess) return HZ_ERR_CUDA;
+  if (err != cudaSuccess) return cuda_err(err);
   const int nb = (int)std::min<long long>((e->ncat * 8 + 255) / 256, 152 * 16);
   k_ens_pack<<<nb, 256, 0, e->st>>>(e->cat_off, e->pad_off, e->tube_of_cat, e->ncat, e->ep.fs, d_prim, e->ep.P0, 1);
   // tube index of every padded cell, staged in the unused ninth field of P1
@@ -529,7 +529,7 @@ int hz_ensemble_set_primitives(hz_ensemble* e, const double* d_prim) {
   if (err == cudaSuccess) err = cudaMemcpyAsync(e->ep.U1, e->ep.U0, e->L.state_b, cudaMemcpyDeviceToDevice, e->st);
   if (err == cudaSuccess) err = cudaMemsetAsync(e->ep.res, 0, sizeof(TubeResult) * e->ntubes, e->st);
   e->have_prim = 1;
-  if (err != cudaSuccess) return HZ_ERR_CUDA;
+  if (err != cudaSuccess) return cuda_err(err);
   return cuda_err(cudaGetLastError());
 }
 
@@ -558,18 +558,18 @@ int hz_ensemble_run(hz_ensemble* e, double t_end, double cfl, long long max_step
   if (!e->graph) {
     cudaGraph_t g = nullptr;
     cudaError_t err = cudaStreamBeginCapture(e->st, cudaStreamCaptureModeThreadLocal);
-    if (err != cudaSuccess) return HZ_ERR_CUDA;
+    if (err != cudaSuccess) return cuda_err(err);
     const int r = ens_launch(e, t_end, cfl, max_steps);
     err = cudaStreamEndCapture(e->st, &g);
     if (r != HZ_OK || err != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
-      return r != HZ_OK ? r : HZ_ERR_CUDA;
+      return r != HZ_OK ? r : cuda_err(err);
     }
     err = cudaGraphInstantiate(&e->graph, g, 0);
     cudaGraphDestroy(g);
     if (err != cudaSuccess) {
       e->graph = nullptr;
-      return HZ_ERR_CUDA;
+      return cuda_err(err);
     }
     e->graph_t_end = t_end;
     e->graph_cfl = cfl;
@@ -592,7 +592,7 @@ int hz_ensemble_results(hz_ensemble* e, double* h_t, long long* h_steps, long lo
   cudaError_t err = cudaMemcpyAsync(r.data(), e->ep.res, sizeof(TubeResult) * e->ntubes,
                                     cudaMemcpyDeviceToHost, e->st);
   if (err == cudaSuccess) err = cudaStreamSynchronize(e->st);
-  if (err != cudaSuccess) return HZ_ERR_CUDA;
+  if (err != cudaSuccess) return cuda_err(err);
   long long tot = 0;
   for (int t = 0; t < e->ntubes; ++t) {
     h_t[t] = r[t].t;
@@ -611,7 +611,11 @@ int hz_ensemble_autotune(hz_ensemble* e, const double* d_prim, double t_probe, d
   if (!e || !d_prim || !h_threads || !h_ctas_per_sm || !(t_probe > 0.0) || !(cfl > 0.0)) return HZ_ERR_ARG;
   const int cand[5][2] = {{64, 4}, {128, 1}, {128, 2}, {128, 3}, {256, 1}};
   cudaEvent_t a, b;
-  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return HZ_ERR_CUDA;
+  if (const cudaError_t ea = cudaEventCreate(&a); ea != cudaSuccess) return cuda_err(ea);
+  if (const cudaError_t eb = cudaEventCreate(&b); eb != cudaSuccess) {
+    cudaEventDestroy(a);
+    return cuda_err(eb);
+  }
   float best = 1e30f;
   int bt = 128, bm = 2;
   for (int k = 0; k < 5; ++k) {
@@ -621,10 +625,11 @@ int hz_ensemble_autotune(hz_ensemble* e, const double* d_prim, double t_probe, d
     cudaEventRecord(a, e->st);
     r = ens_launch(e, t_probe, cfl, 1LL << 40);
     cudaEventRecord(b, e->st);
-    if (r != HZ_OK || cudaEventSynchronize(b) != cudaSuccess) {
+    const cudaError_t es = r != HZ_OK ? cudaSuccess : cudaEventSynchronize(b);
+    if (r != HZ_OK || es != cudaSuccess) {
       cudaEventDestroy(a);
       cudaEventDestroy(b);
-      return r != HZ_OK ? r : HZ_ERR_CUDA;
+      return r != HZ_OK ? r : cuda_err(es);
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);

@@ -36,6 +36,7 @@ struct KParams {
   int c2p_1d;            // 1: the 1D recovery scheme (Newton in z, v^2 eliminated)
   int zlen;              // cells of z per block (the chunked grid of the mixed and pair kernels)
   int nsm;               // SMs of the device the context was created on
+  int dev;               // that device's ordinal
   // Geometry tables of a metric with zero shift and diagonal gamma (filled by hz_set_metric,
   // used by the DIAG kernels), in the metric's padded layout (field stride ms):
   //   geo_c  centre geometry, GEO_C fields (both precisions; FP64 values): the GEO_N fields
@@ -83,6 +84,12 @@ struct StageArgs {
   double a0, ak;
   int last;              // 1 on the last substep: accumulate the CFL maximum
 };
+
+#ifdef __CUDACC__
+// The CUDA runtime error behind an HZ_ERR_CUDA: records e (when it is an error) as the calling
+// host thread's last one (hz_last_cuda_error) and returns HZ_OK or HZ_ERR_CUDA.
+int record_cuda_error(cudaError_t e);
+#endif
 
 // Which instantiation to launch.
 struct Variant {

@@ -405,6 +405,38 @@ __device__ __forceinline__ void hlle_face(const Geom<R>& G, const R PL[9], const
 }
 
 
+// The HLLE flux of the face at i - 1/2 along D of cell (i, j, k) from its reconstructed states
+// PL, PR: the face metric (mean of the two adjacent centre values; tabulated for a DIAG metric
+// in FP64), then hlle_face_fused.
+template <int D, bool CLEAN, bool DIAG, typename R, typename S>
+__device__ __forceinline__ void face_riemann(const KParams& kp, const S* __restrict__ M, int i, int j,
+                                             int k, R PL[9], R PR[9], R* out, int ostride) {
+  if (!CLEAN) PL[8] = PR[8] = R(0);
+  Geom<R> G;
+  if constexpr (DIAG && !SameType<R, float>::value) {
+    G = geo_load<R>(kp.geo_f + D * GEO_F * kp.ms, met_off(kp, i, j, k), kp.ms);
+  } else {
+    R m[10];
+    const long long o1 = met_off(kp, i, j, k);
+    const long long o0 = o1 - (D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane));
+    R m0[10], m1[10];
+    load_metric<DIAG>(kp, M, o0, m0);
+    load_metric<DIAG>(kp, M, o1, m1);
+#pragma unroll
+    for (int f = 0; f < 10; ++f) m[f] = R(0.5) * (m0[f] + m1[f]);
+    G = make_geom<DIAG>(m);
+  }
+  const Consts<R> c = consts_of<R>(kp);
+  R cfac = R(0);
+  if constexpr (CLEAN && DIAG) {
+    if constexpr (!SameType<R, float>::value)
+      cfac = ldc<R>(kp.geo_f + (D * GEO_F + GEO_N) * kp.ms + met_off(kp, i, j, k));
+    else
+      cfac = G.alp * fsqrt(sel<D>(G.ixx, G.iyy, G.izz));
+  }
+  hlle_face_fused<D, CLEAN, DIAG>(G, PL, PR, c, cfac, out, ostride);
+}
+
 // HLLE flux of the face at i - 1/2 along D of cell (i, j, k) (the face between cells i-1 and
 // i along D), written to out[f * ostride].
 // RECON 0: TVD with the MC limiter (stencil c-2 .. c+1); 1: PPM (stencil c-3 .. c+2).
@@ -465,32 +497,64 @@ __device__ __forceinline__ void face_flux(const KParams& kp, const S* __restrict
                   ldc<R>(pf + off[3]), ldc<R>(pf + off[4]), ldc<R>(pf + off[5]), PL[f], PR[f]);
     }
   }
-  if (!CLEAN) PL[8] = PR[8] = R(0);
-  // face metric: mean of the two adjacent centre values (tabulated for a DIAG metric in FP64)
-  Geom<R> G;
-  if constexpr (DIAG && !SameType<R, float>::value) {
-    G = geo_load<R>(kp.geo_f + D * GEO_F * kp.ms, met_off(kp, i, j, k), kp.ms);
-  } else {
-    R m[10];
-    const long long o1 = met_off(kp, i, j, k);
-    const long long o0 = o1 - (D == 0 ? 1 : (D == 1 ? kp.mpitch : kp.mplane));
-    R m0[10], m1[10];
-    load_metric<DIAG>(kp, M, o0, m0);
-    load_metric<DIAG>(kp, M, o1, m1);
-#pragma unroll
-    for (int f = 0; f < 10; ++f) m[f] = R(0.5) * (m0[f] + m1[f]);
-    G = make_geom<DIAG>(m);
-  }
-  const Consts<R> c = consts_of<R>(kp);
-  R cfac = R(0);
-  if constexpr (CLEAN && DIAG) {
-    if constexpr (!SameType<R, float>::value)
-      cfac = ldc<R>(kp.geo_f + (D * GEO_F + GEO_N) * kp.ms + met_off(kp, i, j, k));
-    else
-      cfac = G.alp * fsqrt(sel<D>(G.ixx, G.iyy, G.izz));
-  }
-  hlle_face_fused<D, CLEAN, DIAG>(G, PL, PR, c, cfac, out, ostride);
+  face_riemann<D, CLEAN, DIAG>(kp, M, i, j, k, PL, PR, out, ostride);
 }
+
+// HLLE flux of the face at i - 1/2 along D (0 or 1) of cell (i, j, k), its MC stencil read from
+// a primitive plane staged in shared memory (stage_plane): sp is the stencil's first cell (i - 2
+// along x, j - 2 along y) of field 0, fields sf apart, stencil cells ss apart.  The same
+// operations on the same operands as face_flux's MC stencil.
+template <int D, bool CLEAN, bool DIAG, typename R, typename S>
+__device__ __forceinline__ void face_flux_smem(const KParams& kp, const R* sp, int sf, int ss,
+                                               const S* __restrict__ M, int i, int j, int k, R* out,
+                                               int ostride) {
+  constexpr int NV = CLEAN ? 9 : 8;
+  R PL[9], PR[9];
+#pragma unroll
+  for (int f = 0; f < NV; ++f) {
+    const R* q = sp + f * sf;
+    const R a = q[0], b = q[ss], cc = q[2 * ss], d = q[3 * ss];
+    const R d0 = b - a, d1 = cc - b, d2 = d - cc;
+    PL[f] = b + mc_half_slope(d0, d1);
+    PR[f] = cc - mc_half_slope(d1, d2);
+  }
+  face_riemann<D, CLEAN, DIAG>(kp, M, i, j, k, PL, PR, out, ostride);
+}
+
+#ifdef __CUDACC__
+// Asynchronous 4-byte copy from global to shared memory (cp.async, cached in L1), the commit of
+// the copies a thread has issued, and the wait for all of them.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Stage plane k of the FP32 primitive state for the TX x TY tile at (i0, j0): sp[f][ly][lx] with
+// SX = TX + 4 columns and SY = TY + 4 rows, local (lx, ly) = global (i0 - 2 + lx, j0 - 2 + ly),
+// boundary indices resolved as face_flux resolves them (clamped or wrapped).  Only the cells some
+// x or y face of the tile reads are copied (up to the tile's last face + 1 along each axis, which
+// for a ragged tile stops inside [-2, n + 1], where bc_index is valid).  Copies are asynchronous;
+// the caller waits (cp_async_wait_all) and synchronises the block before reading.
+template <int TX, int TY, int NV>
+__device__ __forceinline__ void stage_plane(const KParams& kp, const float* __restrict__ P, float* sp,
+                                            int i0, int j0, int k) {
+  constexpr int SX = TX + 4, SY = TY + 4, SF = SX * SY;
+  const int nxl = min(TX, kp.nx - i0) + 4, nyl = min(TY, kp.ny - j0) + 4;
+  const float* pk = P + (long long)k * kp.plane;
+  for (int e = threadIdx.x; e < SF; e += TX * TY) {
+    const int ly = e / SX, lx = e - ly * SX;
+    if (lx < nxl && ly < nyl) {
+      const int ii = bc_index(i0 - 2 + lx, kp.nx, kp.bcx), jj = bc_index(j0 - 2 + ly, kp.ny, kp.bcy);
+      const float* src = pk + (long long)jj * kp.pitch + ii;
+#pragma unroll
+      for (int f = 0; f < NV; ++f) cp_async4(sp + f * SF + e, src + f * kp.fs);
+    }
+  }
+  cp_async_commit();
+}
+#endif  // __CUDACC__
 
 // One face of the double-word path with its direction D given at run time (one copy of the
 // face code for all three directions): the stencil runs along D, and vectors and the metric are
@@ -713,22 +777,15 @@ __device__ __forceinline__ void block_stats(DevScalars* sc, double vloc, int nfa
 }
 #endif  // __CUDACC__
 
-// Recovery with atmosphere / floor handling; rewrites U when the cell is reset.  TG, TP: the
-// element types of the guess and of the result (float for the mixed path, whose primitive
-// state is stored in FP32; a pressure-floor reset recomputes U from that stored state).
-// atm_b2: when not null and the cell is set to the atmosphere, receives that state's b^2.
-template <bool CLEAN, bool DIAG, bool ONE_FINISH = false, typename TG = double, typename TP = double>
-__device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G, double U[9],
-                                       const TG Pg[9], const Consts<double>& c, TP P[9],
-                                       int& iters, double* atm_b2 = nullptr) {
-  // atmosphere: a cell whose rest-mass density D / sqrt(gamma) = rho W is below rho_atm is not
-  // recovered but set to the atmosphere state (the decision uses the conserved state only)
-  const bool atm = U[U_D] < kp.rho_atm * G.sqrtg;
-  C2PResult r = {1, 0};
-  if (!atm)
-    r = con2prim<CLEAN, DIAG, ONE_FINISH, TG, TP>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_step_tol, P, kp.c2p_1d);
-  iters = r.iters;
-  if (atm || !r.ok || (double)P[P_RHO] < kp.rho_floor) {
+// Reset of a cell the recovery does not accept (§3.2 names no rule; the atmosphere and floors of
+// the method's readings).  to_atm: the atmosphere state; else the recovered state with its
+// pressure raised to p_floor.  Rewrites P and U.  atm_b2: when not null and the cell is set to
+// the atmosphere, receives that state's b^2.
+template <bool CLEAN, bool DIAG, typename TP>
+__device__ __forceinline__ void reset_cell(const KParams& kp, const Geom<double>& G, double U[9],
+                                           const Consts<double>& c, TP P[9], bool to_atm,
+                                           double* atm_b2) {
+  if (to_atm) {
     // The atmosphere state: rho_floor, p_atm, u~ = 0, the cell's B and psi.  Its conserved
     // vector in closed form: u~ = 0 gives W = 1, u^t = 1/alpha, u_i = 0 and b^t = 0, hence
     // b^i = alpha B^i and b^2 = gamma_ij Bn^i Bn^j with the Eulerian field Bn^i = alpha B^i =
@@ -757,7 +814,7 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
     U[U_TT] = -G.sqrtmg * fma(0.5, b2, e_atm);
     U[U_TX] = U[U_TY] = U[U_TZ] = 0.0;
     if (atm_b2) *atm_b2 = b2;
-  } else if ((double)P[P_PRS] < kp.p_floor) {
+  } else {
     P[P_PRS] = (TP)kp.p_floor;
     double Pd[9];
 #pragma unroll
@@ -765,8 +822,101 @@ __device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G,
     const State<double> S = make_state<DIAG>(G, Pd, c);
     cons_of<CLEAN>(G, S, U);
   }
+}
+
+// Recovery with atmosphere / floor handling; rewrites U when the cell is reset.  TG, TP: the
+// element types of the guess and of the result (float for the mixed path, whose primitive
+// state is stored in FP32; a pressure-floor reset recomputes U from that stored state).
+// atm_b2: when not null and the cell is set to the atmosphere, receives that state's b^2.
+template <bool CLEAN, bool DIAG, bool ONE_FINISH = false, typename TG = double, typename TP = double>
+__device__ __forceinline__ int recover(const KParams& kp, const Geom<double>& G, double U[9],
+                                       const TG Pg[9], const Consts<double>& c, TP P[9],
+                                       int& iters, double* atm_b2 = nullptr) {
+  // atmosphere: a cell whose rest-mass density D / sqrt(gamma) = rho W is below rho_atm is not
+  // recovered but set to the atmosphere state (the decision uses the conserved state only)
+  const bool atm = U[U_D] < kp.rho_atm * G.sqrtg;
+  C2PResult r = {1, 0};
+  if (!atm)
+    r = con2prim<CLEAN, DIAG, ONE_FINISH, TG, TP>(G, U, Pg, c, kp.c2p_maxit, kp.c2p_step_tol, P, kp.c2p_1d);
+  iters = r.iters;
+  if (atm || !r.ok || (double)P[P_RHO] < kp.rho_floor)
+    reset_cell<CLEAN, DIAG>(kp, G, U, c, P, true, atm_b2);
+  else if ((double)P[P_PRS] < kp.p_floor)
+    reset_cell<CLEAN, DIAG>(kp, G, U, c, P, false, nullptr);
   return r.ok ? 0 : 1;
 }
+
+#ifdef __CUDACC__
+// Inputs of an out-of-line recovery (con2prim_call).
+template <typename TG>
+struct C2PArgs {
+  Geom<double> G;
+  Consts<double> c;
+  double U[9];
+  TG Pg[9];
+  double step_tol;
+  int maxit, one_d;
+};
+
+// con2prim as a function of its own (not inlined): a kernel whose cells mostly skip the Newton
+// iteration (atmosphere) then reserves no registers for it, and the iteration's live values are
+// saved and restored only on the path that calls it.
+template <bool CLEAN, bool DIAG, bool ONE_FINISH, typename TG, typename TP>
+static __device__ __noinline__ C2PResult con2prim_call(const C2PArgs<TG>* a, TP* P) {
+  return con2prim<CLEAN, DIAG, ONE_FINISH, TG, TP>(a->G, a->U, a->Pg, a->c, a->maxit, a->step_tol, P, a->one_d);
+}
+
+// recover() for a kernel that stores the conserved vector itself: U is written to Uout (field
+// stride fs) before the Newton iteration, which runs out of line (con2prim_call), and again,
+// reloaded and rewritten, only for a cell that is then reset.  Same results as recover()
+// followed by the store of U.
+template <bool CLEAN, bool DIAG, bool ONE_FINISH, typename TG, typename TP>
+__device__ __forceinline__ int recover_stored(const KParams& kp, const Geom<double>& G, double U[9],
+                                              double* Uout, long long fs, const TG Pg[9],
+                                              const Consts<double>& c, TP P[9], int& iters,
+                                              double* atm_b2 = nullptr) {
+  constexpr int NV = CLEAN ? 9 : 8;
+  const bool atm = U[U_D] < kp.rho_atm * G.sqrtg;
+  C2PResult r = {1, 0};
+  bool to_atm = atm;
+  if (!atm) {
+#pragma unroll
+    for (int f = 0; f < NV; ++f) Uout[f * fs] = U[f];
+    {
+      C2PArgs<TG> a;
+      a.G = G;
+      a.c = c;
+#pragma unroll
+      for (int f = 0; f < 9; ++f) {
+        a.U[f] = U[f];
+        a.Pg[f] = Pg[f];
+      }
+      a.step_tol = kp.c2p_step_tol;
+      a.maxit = kp.c2p_maxit;
+      a.one_d = kp.c2p_1d;
+      TP Pr[9];
+      r = con2prim_call<CLEAN, DIAG, ONE_FINISH, TG, TP>(&a, Pr);
+#pragma unroll
+      for (int f = 0; f < 9; ++f) P[f] = Pr[f];
+    }
+    to_atm = !r.ok || (double)P[P_RHO] < kp.rho_floor;
+    if (!to_atm && !((double)P[P_PRS] < kp.p_floor)) {
+      iters = r.iters;
+      return 0;
+    }
+    // a reset after the iteration: the conserved vector back from memory (an opaque load, so
+    // that the compiler does not keep it in registers through the iteration)
+#pragma unroll
+    for (int f = 0; f < NV; ++f)
+      asm volatile("ld.global.f64 %0, [%1];" : "=d"(U[f]) : "l"(Uout + f * fs) : "memory");
+  }
+  iters = r.iters;
+  reset_cell<CLEAN, DIAG>(kp, G, U, c, P, to_atm, to_atm ? atm_b2 : nullptr);
+#pragma unroll
+  for (int f = 0; f < NV; ++f) Uout[f * fs] = U[f];
+  return r.ok ? 0 : 1;
+}
+#endif  // __CUDACC__
 
 #ifdef __CUDACC__
 // PAIR (FP64 state only): reconstruction, face states, fluxes, HLLE, divergence and sources in
@@ -791,6 +941,12 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   constexpr bool ZCARRY = ZA && !PAIR && RECON == 0;
   extern __shared__ __align__(16) unsigned char hz_dyn_smem[];
   R* const zc = reinterpret_cast<R*>(hz_dyn_smem) + threadIdx.x;
+  // Mixed 3-D MC kernels: the primitive plane that the x and y faces read (the tile with a
+  // two-cell halo) is staged in shared memory by asynchronous copies (stage_plane), behind the
+  // carry; the copies of plane k + 1 are issued before the cell update of plane k and overlap it.
+  constexpr bool STAGE = MIXED && YA && ZA && RECON == 0 && !PAIR;
+  constexpr int SX = TX + 4, SF = (TX + 4) * (TY + 4);
+  R* const sp = reinterpret_cast<R*>(hz_dyn_smem + (ZCARRY ? 3 * NV * NT * sizeof(R) : 0));
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const double dt = sc->dt;
@@ -837,6 +993,9 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   const int i = i0 + tx, j = j0 + ty;
   const bool own = i < kp.nx && j < kp.ny;
 
+#ifdef __CUDACC__
+  if constexpr (STAGE) stage_plane<TX, TY, NV>(kp, P, sp, i0, j0, kz0);
+#endif
   if constexpr (!PAIR) {
     if (ZA && own) {
       if constexpr (ZCARRY)
@@ -844,6 +1003,10 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       else
         face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, kz0, &fz[kz0 & 1][0][ty][tx], TY * TX);
     }
+  }
+  if constexpr (STAGE) {
+    cp_async_wait_all();
+    __syncthreads();
   }
 
   for (int k = kz0; k < kz1; ++k) {
@@ -902,6 +1065,29 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         }
         if (D >= 0) face_flux_dw<CLEAN, DIAG>(kp, P, M, D, ii, jj, kk, o, os);
       }
+    } else if constexpr (STAGE) {
+      // x and y faces from the staged plane; z faces as below
+      if (i <= kp.nx && j < kp.ny)
+        face_flux_smem<0, CLEAN, DIAG>(kp, sp + (ty + 2) * SX + tx, SF, 1, M, i, j, k, &fx[0][ty][tx], TY * (TX + 1));
+      if (i < kp.nx && j <= kp.ny)
+        face_flux_smem<1, CLEAN, DIAG>(kp, sp + ty * SX + tx + 2, SF, SX, M, i, j, k, &fy[0][ty][tx], (TY + 1) * TX);
+      if (own) {
+        if constexpr (ZCARRY)
+          face_flux<2, CLEAN, DIAG, RECON, 2>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX, zc, NT);
+        else
+          face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
+      }
+      if (threadIdx.x < TX) {
+        const int ii = i0 + threadIdx.x, jj = j0 + TY;
+        if (ii < kp.nx && jj <= kp.ny)
+          face_flux_smem<1, CLEAN, DIAG>(kp, sp + TY * SX + threadIdx.x + 2, SF, SX, M, ii, jj, k,
+                                         &fy[0][TY][threadIdx.x], (TY + 1) * TX);
+      } else if (threadIdx.x >= 32 && threadIdx.x < 32 + TY) {
+        const int t = threadIdx.x - 32, jj = j0 + t, ii = i0 + TX;
+        if (ii <= kp.nx && jj < kp.ny)
+          face_flux_smem<0, CLEAN, DIAG>(kp, sp + (t + 2) * SX + TX, SF, 1, M, ii, jj, k, &fx[0][t][TX],
+                                         TY * (TX + 1));
+      }
     } else {
     if (i <= kp.nx && j < kp.ny) face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, i, j, k, &fx[0][ty][tx], TY * (TX + 1));
     if (YA && i < kp.nx && j <= kp.ny) face_flux<1, CLEAN, DIAG, RECON>(kp, P, M, i, j, k, &fy[0][ty][tx], (TY + 1) * TX);
@@ -928,7 +1114,20 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x][TX], TY * (TX + 1));
     }
     }
+    // the cell's own primitive state from the staged plane, before the next plane replaces it
+    R Pcs[9];
+    if constexpr (STAGE) {
+      if (own) {
+#pragma unroll
+        for (int f = 0; f < NV; ++f) Pcs[f] = sp[f * SF + (ty + 2) * SX + tx + 2];
+      }
+    }
     __syncthreads();
+#ifdef __CUDACC__
+    if constexpr (STAGE) {
+      if (k + 1 < kz1) stage_plane<TX, TY, NV>(kp, P, sp, i0, j0, k + 1);
+    }
+#endif
 
     // ---- cell update of plane k
     if (own) {
@@ -953,7 +1152,10 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       }
       R Pc[9];
 #pragma unroll
-      for (int f = 0; f < NV; ++f) Pc[f] = ldc<R>(P + f * kp.fs + off);
+      for (int f = 0; f < NV; ++f) {
+        if constexpr (STAGE) Pc[f] = Pcs[f];
+        else Pc[f] = ldc<R>(P + f * kp.fs + off);
+      }
       if (!CLEAN) Pc[8] = R(0);
       {
         const State<R> St = make_state<DIAG>(G, Pc, c);
@@ -1033,8 +1235,28 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
           load_metric<DIAG>(kp, M, mo, md);
           Gd = make_geom<DIAG>(md);
         }
-        nfail += recover<CLEAN, DIAG, true, R, R>(kp, Gd, U, Pc, cd, Pn, it);
-        if (sa.last) vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pn, c));
+        // the conserved vector is stored by the recovery (recover_stored), and the FP32 centre
+        // geometry of the CFL speeds is formed again after it: neither is held in registers
+        // through the Newton iteration
+        nfail += recover_stored<CLEAN, DIAG, true>(kp, Gd, U, sa.Uout + off, kp.fs, Pc, cd, Pn, it);
+        if (sa.last) {
+          R mc[10];
+#pragma unroll
+          for (int f = 0; f < 10; ++f) mc[f] = R(0);
+          if constexpr (DIAG) {
+            const S* mp = M + mo;
+            asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(mc[M_ALP]) : "l"(mp + M_ALP * kp.ms));
+            asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(mc[M_GXX]) : "l"(mp + M_GXX * kp.ms));
+            asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(mc[M_GYY]) : "l"(mp + M_GYY * kp.ms));
+            asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(mc[M_GZZ]) : "l"(mp + M_GZZ * kp.ms));
+          } else {
+#pragma unroll
+            for (int f = 0; f < 10; ++f)
+              asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(mc[f]) : "l"(M + mo + f * kp.ms));
+          }
+          const Geom<R> Gc = make_geom<DIAG>(mc);
+          vloc = fmax(vloc, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, Gc, Pn, c));
+        }
       } else {
         double ab2 = -1.0;
         nfail += recover<CLEAN, DIAG>(kp, G, U, Pc, cd, Pn, it, DIAG ? &ab2 : nullptr);
@@ -1048,10 +1270,11 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       maxit = max(maxit, it);
 #pragma unroll
       for (int f = 0; f < NV; ++f) {
-        sa.Uout[f * kp.fs + off] = U[f];
+        if constexpr (!MIXED) sa.Uout[f * kp.fs + off] = U[f];  // mixed: stored by recover_stored
         Pout[f * kp.fs + off] = (S)Pn[f];
       }
     }
+    if constexpr (STAGE) cp_async_wait_all();  // plane k + 1 staged before the barrier
     __syncthreads();
   }
   }  // z segments of this block
@@ -1125,7 +1348,12 @@ template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED, i
 void launch_substep_one(const KParams& kp, const StageArgs& sa, const typename Prec<MIXED>::S* M,
                         DevScalars* sc, size_t dyn, int zchunks, cudaStream_t st) {
   auto kern = k_substep<TX, TY, YA, ZA, CLEAN, DIAG, MIXED, RECON, PAIR>;
-  static int per_sm = 0;  // one per instantiation
+  // once per instantiation and device (function attributes are per device): the dynamic shared
+  // memory opt-in and the resident blocks per SM.  The context's device is the current one.
+  constexpr int kMaxDev = 64;
+  static int per_sm_of[kMaxDev] = {};
+  const int dv = kp.dev >= 0 && kp.dev < kMaxDev ? kp.dev : 0;
+  int& per_sm = per_sm_of[dv];
   if (per_sm == 0) {
     if (dyn) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int nb = 0;
@@ -1160,7 +1388,10 @@ void launch_substep_t(const Variant& v, const KParams& kp, const StageArgs& sa, 
   const S* M = (const S*)Mv;
   // dynamic shared memory: the z-face reconstruction carry of the MC kernels (k_substep)
   constexpr bool ZCARRY = ZA && !PAIR && RECON == 0;
-  const size_t dyn = ZCARRY ? (size_t)3 * (v.clean ? 9 : 8) * TX * TY * sizeof(R) : 0;
+  // and, for the mixed 3-D MC kernels, the staged primitive plane
+  constexpr bool STAGE = MIXED && YA && ZA && RECON == 0 && !PAIR;
+  const size_t dyn = (ZCARRY ? (size_t)3 * (v.clean ? 9 : 8) * TX * TY * sizeof(R) : 0) +
+                     (STAGE ? (size_t)(v.clean ? 9 : 8) * (TX + 4) * (TY + 4) * sizeof(float) : 0);
   if (v.clean) {
     if (v.diag) launch_substep_one<TX, TY, YA, ZA, true, true, MIXED, RECON, PAIR>(kp, sa, M, sc, dyn, zchunks, st);
     else launch_substep_one<TX, TY, YA, ZA, true, false, MIXED, RECON, PAIR>(kp, sa, M, sc, dyn, zchunks, st);

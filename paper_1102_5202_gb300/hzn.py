@@ -32,7 +32,7 @@ EXPORTED = (
     "hz_workspace_bytes", "hz_create", "hz_destroy", "hz_set_metric", "hz_set_primitives",
     "hz_get_primitives", "hz_get_conserved", "hz_step", "hz_step_cfl", "hz_max_speed",
     "hz_get_stats", "hz_strerror", "hz_version", "hz_step_noalloc", "hz_dw_selftest",
-    "hz_rcp_selftest",
+    "hz_rcp_selftest", "hz_last_cuda_error", "hz_cuda_error_string",
 )
 HZ_DW_NRESULTS = 9
 
@@ -76,7 +76,12 @@ _lib = None
 
 class HznError(RuntimeError):
     def __init__(self, code: int, call: str):
-        super().__init__(f"{call} failed: {code} ({hz_strerror(code)})")
+        msg = f"{call} failed: {code} ({hz_strerror(code)})"
+        self.cuda_code = 0
+        if code == HZ_ERR_CUDA:
+            self.cuda_code = int(lib().hz_last_cuda_error())
+            msg += f"; CUDA error {self.cuda_code}: {lib().hz_cuda_error_string(self.cuda_code).decode()}"
+        super().__init__(msg)
         self.code = code
 
 
@@ -113,8 +118,11 @@ def lib():
             L.hz_strerror.argtypes = [ctypes.c_int]
             L.hz_strerror.restype = ctypes.c_char_p
             L.hz_version.restype = ctypes.c_int
+            L.hz_last_cuda_error.argtypes = []
+            L.hz_cuda_error_string.argtypes = [ctypes.c_int]
+            L.hz_cuda_error_string.restype = ctypes.c_char_p
             for name in EXPORTED:
-                if name not in ("hz_strerror", "hz_version"):
+                if name not in ("hz_strerror", "hz_version", "hz_cuda_error_string"):
                     getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib

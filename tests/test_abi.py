@@ -40,6 +40,29 @@ def test_strerror_names_every_code(lib):
     assert hzn.hz_strerror(-99) == "unknown code"
 
 
+def test_cuda_error_query(lib):
+    """hz_last_cuda_error starts at 0 on a thread that met no CUDA error (argument errors are
+    not CUDA errors), and hz_cuda_error_string describes CUDA runtime codes."""
+    import threading
+
+    seen = []
+
+    def probe():
+        seen.append(int(lib.hz_last_cuda_error()))
+        g = hzn.make_grid((0, 1, 1), (0.1, 1.0, 1.0), (0, 0, 0))
+        o = hzn.make_options(2.0)
+        n = ctypes.c_size_t(0)
+        seen.append(int(lib.hz_workspace_bytes(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n))))
+        seen.append(int(lib.hz_last_cuda_error()))
+
+    t = threading.Thread(target=probe)
+    t.start()
+    t.join()
+    assert seen == [0, hzn.HZ_ERR_ARG, 0]
+    assert lib.hz_cuda_error_string(0).decode() == "no error"
+    assert "argument" in lib.hz_cuda_error_string(1).decode()
+
+
 def test_workspace_bytes_and_argument_checks(lib):
     g = hzn.make_grid((192, 192, 192), (0.2, 0.2, 0.2), (0, 0, 0))
     o = hzn.make_options(2.0, cleaning=True, ch=0.5, kappa=1.0)
