@@ -58,15 +58,15 @@ ALG_FLOPS_PER_ZU_FP64_PHASES = 308.66399468315973
 # blob (profiles/k_substep_blob3d.md): DFMA counted as 2 flops, DADD/DMUL as 1.  Reported
 # beside the algorithmic rate: the kernel's own arithmetic (reciprocal refinements, the
 # recovery's corrections) differs from the method's count.
-FP64_FLOPS_PER_CELL_SUBSTEP = 1525.1
+FP64_FLOPS_PER_CELL_SUBSTEP = 1502.6
 # FP64 instructions (DFMA + DMUL + DADD) per cell per substep from the same capture, and the
 # FP64 instruction rate of the pipe measured by the probe (1.91 DFMA per clock per SM at
 # 2070 MHz): DMUL and DADD occupy the pipe like a DFMA, so this fraction is the pipe's use.
-FP64_INST_PER_CELL_SUBSTEP = 1189.7
+FP64_INST_PER_CELL_SUBSTEP = 1171.8
 FP64_INST_PEAK_PER_S = 6.0e11
 # DRAM bytes per cell per substep of the same kernel from the same capture (read + write,
-# 1506 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
-DRAM_BYTES_PER_CELL_SUBSTEP = 718.0
+# 2094 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
+DRAM_BYTES_PER_CELL_SUBSTEP = 998.6
 # The same two figures for the mixed-precision substep kernel at 192^3
 # (profiles/k_substep_mixed_blob3d.md): FP64 flops (recovery, update) per cell per substep,
 # and DRAM bytes per cell per substep.
