@@ -743,6 +743,22 @@ __device__ __forceinline__ double atm_cfl_rate(const KParams& kp, double b2, dou
   return c * cfl_geo;
 }
 
+// Which warps of a TX x TY tile compute its extra faces on plane k: the top row of y faces (one
+// full warp pass, warp wy) and the right column of x faces (TY lanes of warp wx).  A warp's FP64
+// instruction holds the FP64 pipe for the same time whatever its active lanes, so each job costs
+// its warp a full face pass; ROTATE moves both jobs one warp along per plane, so that over NW
+// planes every warp carries the same number of passes.
+template <int NW, bool ROTATE>
+__host__ __device__ __forceinline__ void extra_warps(int k, int& wy, int& wx) {
+  static_assert((NW & (NW - 1)) == 0, "a power of two warps");
+  if constexpr (NW < 2) {  // one warp (1-D tiles): no extra faces of this kind
+    wy = wx = 0;
+  } else {
+    wy = ROTATE ? (k & (NW - 1)) : 0;
+    wx = ROTATE ? ((k + NW / 2) & (NW - 1)) : 1;
+  }
+}
+
 #ifdef __CUDACC__  // device-only: block reduction, kernels, launchers (the helpers build for the host too)
 // Block reduction of the CFL maximum, the failure count and the largest iteration count.
 template <int NT>
@@ -946,6 +962,7 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   // carry; the copies of plane k + 1 are issued before the cell update of plane k and overlap it.
   constexpr bool STAGE = MIXED && YA && ZA && RECON == 0 && !PAIR;
   constexpr int SX = TX + 4, SF = (TX + 4) * (TY + 4);
+  constexpr bool ROTATE = true;
   R* const sp = reinterpret_cast<R*>(hz_dyn_smem + (ZCARRY ? 3 * NV * NT * sizeof(R) : 0));
 
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -1077,13 +1094,17 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         else
           face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
       }
-      if (threadIdx.x < TX) {
-        const int ii = i0 + threadIdx.x, jj = j0 + TY;
+      // the tile's extra faces, on warps that change with the plane (extra_warps)
+      int wy, wx;
+      extra_warps<NT / 32, ROTATE>(k, wy, wx);
+      const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      if (wid == wy) {
+        const int ii = i0 + lane, jj = j0 + TY;
         if (ii < kp.nx && jj <= kp.ny)
-          face_flux_smem<1, CLEAN, DIAG>(kp, sp + TY * SX + threadIdx.x + 2, SF, SX, M, ii, jj, k,
-                                         &fy[0][TY][threadIdx.x], (TY + 1) * TX);
-      } else if (threadIdx.x >= 32 && threadIdx.x < 32 + TY) {
-        const int t = threadIdx.x - 32, jj = j0 + t, ii = i0 + TX;
+          face_flux_smem<1, CLEAN, DIAG>(kp, sp + TY * SX + lane + 2, SF, SX, M, ii, jj, k,
+                                         &fy[0][TY][lane], (TY + 1) * TX);
+      } else if (wid == wx && lane < TY) {
+        const int t = lane, jj = j0 + t, ii = i0 + TX;
         if (ii <= kp.nx && jj < kp.ny)
           face_flux_smem<0, CLEAN, DIAG>(kp, sp + (t + 2) * SX + TX, SF, 1, M, ii, jj, k, &fx[0][t][TX],
                                          TY * (TX + 1));
@@ -1098,15 +1119,19 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         face_flux<2, CLEAN, DIAG, RECON>(kp, P, M, i, j, k + 1, &fz[(k + 1) & 1][0][ty][tx], TY * TX);
     }
     if (YA) {
-      // top row of y-faces of the tile: warp 0; right column of x-faces: warp 1
-      if (threadIdx.x < TX) {
-        const int ii = i0 + threadIdx.x, jj = j0 + TY;
+      // the tile's extra faces (top row of y faces, right column of x faces), on warps that
+      // change with the plane (extra_warps)
+      int wy, wx;
+      extra_warps<NT / 32, ROTATE>(k, wy, wx);
+      const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      if (wid == wy) {
+        const int ii = i0 + lane, jj = j0 + TY;
         if (ii < kp.nx && jj <= kp.ny)
-          face_flux<1, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fy[0][TY][threadIdx.x], (TY + 1) * TX);
-      } else if (threadIdx.x >= 32 && threadIdx.x < 32 + TY) {
-        const int jj = j0 + (threadIdx.x - 32), ii = i0 + TX;
+          face_flux<1, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fy[0][TY][lane], (TY + 1) * TX);
+      } else if (wid == wx && lane < TY) {
+        const int jj = j0 + lane, ii = i0 + TX;
         if (ii <= kp.nx && jj < kp.ny)
-          face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fx[0][threadIdx.x - 32][TX], TY * (TX + 1));
+          face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fx[0][lane][TX], TY * (TX + 1));
       }
     } else if (threadIdx.x < TY) {
       const int jj = j0 + threadIdx.x, ii = i0 + TX;
@@ -1341,7 +1366,8 @@ inline int blocks_for(long long n, int threads) {
 
 // One substep launch.  FP64 kernels run on a persistent grid: as many blocks as are resident at
 // once (blocks per SM from the occupancy calculator, once per instantiation, times the SMs),
-// each taking an equal share of the plane-tiles, but at least 8 plane-tiles per block.  Mixed
+// each taking an equal share of the plane-tiles, but at least 8 plane-tiles per block in 3-D
+// and one tile in 1-D and 2-D.  Mixed
 // and double-word kernels: one block per tile column and z chunk.  dyn: the dynamic shared
 // memory (the z-face carry of the MC kernels).
 template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED, int RECON, bool PAIR>
@@ -1368,7 +1394,10 @@ void launch_substep_one(const KParams& kp, const StageArgs& sa, const typename P
   }
   const long long total = (long long)((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY) * kp.nz;
   long long g = (long long)per_sm * (kp.nsm > 0 ? kp.nsm : 1);
-  const long long cap = (total + 7) / 8;
+  // 3-D: at least 8 plane-tiles per block (a z segment's first face costs a full stencil);
+  // 1-D and 2-D (one plane): at least one tile per block, so that a small grid spreads over
+  // as many SMs as it has tiles
+  const long long cap = ZA ? (total + 7) / 8 : total;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   kern<<<(unsigned)g, TX * TY, dyn, st>>>(kp, sa, M, sc);
