@@ -952,6 +952,14 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   __shared__ R fx[NV][TY][TX + 1];
   __shared__ R fy[YA ? NV : 1][YA ? TY + 1 : 1][TX];
   __shared__ R fz[ZA ? 2 : 1][ZA ? NV : 1][TY][TX];
+  // 3-D kernels that read their faces from global memory: the tile's right column of x faces
+  // (TY per plane) is computed for XB planes at once, one lane per face, every XB planes of a z
+  // segment, and kept here (a warp's FP64 instruction costs the same pipe time with TY active
+  // lanes as with 32, so one batched pass replaces XB passes)
+  constexpr bool XBATCH = ZA && YA && !PAIR && !(MIXED && RECON == 0);
+  constexpr int XB = 32 / TY;
+  static_assert(32 % TY == 0, "whole planes of x faces per warp");
+  __shared__ R fxr[XBATCH ? XB : 1][XBATCH ? TY : 1][XBATCH ? NV : 1];
   // z-face reconstruction carry (face_flux ZC), three values per field and thread, in dynamic
   // shared memory (it does not fit the 48 KB of static shared memory beside the face fluxes)
   constexpr bool ZCARRY = ZA && !PAIR && RECON == 0;
@@ -1128,10 +1136,18 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
         const int ii = i0 + lane, jj = j0 + TY;
         if (ii < kp.nx && jj <= kp.ny)
           face_flux<1, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fy[0][TY][lane], (TY + 1) * TX);
-      } else if (wid == wx && lane < TY) {
-        const int jj = j0 + lane, ii = i0 + TX;
-        if (ii <= kp.nx && jj < kp.ny)
-          face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fx[0][lane][TX], TY * (TX + 1));
+      } else if (wid == wx) {
+        if constexpr (XBATCH) {
+          if ((k - kz0) % XB == 0) {  // the right x faces of planes k .. k + XB - 1
+            const int kk = k + lane / TY, jj = j0 + lane % TY, ii = i0 + TX;
+            if (kk < kz1 && ii <= kp.nx && jj < kp.ny)
+              face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, kk, &fxr[lane / TY][lane % TY][0], 1);
+          }
+        } else if (lane < TY) {
+          const int jj = j0 + lane, ii = i0 + TX;
+          if (ii <= kp.nx && jj < kp.ny)
+            face_flux<0, CLEAN, DIAG, RECON>(kp, P, M, ii, jj, k, &fx[0][lane][TX], TY * (TX + 1));
+        }
       }
     } else if (threadIdx.x < TY) {
       const int jj = j0 + threadIdx.x, ii = i0 + TX;
@@ -1161,7 +1177,11 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       R L[9];
 #pragma unroll
       for (int f = 0; f < NV; ++f) {
-        R v = -(fx[f][ty][tx + 1] - fx[f][ty][tx]) * ridx;
+        R fr = fx[f][ty][tx + 1];
+        if constexpr (XBATCH) {
+          if (tx == TX - 1) fr = fxr[(k - kz0) % XB][ty][f];
+        }
+        R v = -(fr - fx[f][ty][tx]) * ridx;
         if (YA) v -= (fy[f][ty + 1][tx] - fy[f][ty][tx]) * ridy;
         if (ZA) v -= (fz[(k + 1) & 1][f][ty][tx] - fz[k & 1][f][ty][tx]) * ridz;
         L[f] = v;

@@ -135,3 +135,26 @@ def test_mixed_3d_staged_plane_tiles(n, bc, clean):
     assert gs["fails"] == 0
     assert_parity(gp, op, TOL_MIXED_ONE_STEP, fields=range(9 if clean else 8),
                   what=f"staged mixed {n} bc={bc} clean={clean}")
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_mixed_atmosphere_threshold_and_floors(axis):
+    """The mixed path's resets: expansion into a near vacuum (the right state below the
+    atmosphere threshold; the expanding gas crosses the threshold and the density and pressure
+    floors, so recovered cells are reset after the iteration, which rewrites their conserved
+    vector), along x in 2-D and along z in 3-D, against the oracle at the mixed one-step bar."""
+    from parity import tile_tube
+
+    left = dict(rho=1.0, p=1.0)
+    right = dict(rho=1e-13, p=1e-15)
+    P = tile_tube(W.shock_tube(64, left, right, 5.0 / 3.0, 0.1), axis)
+    P.rho_floor, P.rho_atm, P.p_floor = 1e-13, 1e-11, 1e-16
+    dt = 2e-3
+    gp, gc, gs = gpu_run(P, nsteps=4, dt=dt, solver=_mixed(P))
+    op, oc, os_ = oracle_run(P, nsteps=4, dt=dt)
+    assert gs["fails"] == 0 and os_["fails"] == 0
+    assert_parity(gp, op, TOL_MIXED_ONE_STEP, fields=range(8), what=f"mixed atmosphere axis {axis}")
+    # conserved vector too: a reset cell's rewritten U is what the oracle's reset gives
+    assert_parity(gc, oc, TOL_MIXED_ONE_STEP, fields=range(8), what=f"mixed atmosphere U axis {axis}")
+    tail = gp[0].reshape(-1, 64)[:, -8:] if axis == 0 else gp[0].reshape(64, -1)[-8:]
+    assert np.allclose(tail, 1e-13, rtol=1e-7, atol=0)
