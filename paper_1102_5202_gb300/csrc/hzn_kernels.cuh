@@ -955,7 +955,8 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   // 3-D kernels that read their faces from global memory: the tile's right column of x faces
   // (TY per plane) is computed for XB planes at once, one lane per face, every XB planes of a z
   // segment, and kept here (a warp's FP64 instruction costs the same pipe time with TY active
-  // lanes as with 32, so one batched pass replaces XB passes)
+  // lanes as with 32, so one batched pass replaces XB passes).  The staged mixed kernel, which
+  // is bound by latency rather than by a pipe, keeps one pass per plane (batched: -1.8 %).
   constexpr bool XBATCH = ZA && YA && !PAIR && !(MIXED && RECON == 0);
   constexpr int XB = 32 / TY;
   static_assert(32 % TY == 0, "whole planes of x faces per warp");
