@@ -65,8 +65,8 @@ FP64_FLOPS_PER_CELL_SUBSTEP = 1502.6
 FP64_INST_PER_CELL_SUBSTEP = 1171.8
 FP64_INST_PEAK_PER_S = 6.0e11
 # DRAM bytes per cell per substep of the same kernel from the same capture (read + write,
-# 2094 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
-DRAM_BYTES_PER_CELL_SUBSTEP = 998.6
+# 2180 MB per launch at 128^3, the geometry tables included), scaled by the cell count.
+DRAM_BYTES_PER_CELL_SUBSTEP = 1039.6
 # The same two figures for the mixed-precision substep kernel at 192^3
 # (profiles/k_substep_mixed_blob3d.md): FP64 flops (recovery, update) per cell per substep,
 # and DRAM bytes per cell per substep.
@@ -633,7 +633,7 @@ def run_e2e(s, P, args, dist, local):
             "dev_out": torch.empty(host_in.shape, dtype=torch.float64, device=s.device),
             "host_out": torch.empty_like(host_in).pin_memory(),
         })
-    nsteps = max(4, min(args.steps, 10))
+    nsteps = max(4, min(args.steps, 20))
     nsteps += nsteps % 2
 
     def one(L):
