@@ -733,14 +733,20 @@ __device__ __forceinline__ double cell_max_speed(const KParams& kp, const Geom<R
 // C = -c^2 gamma^dd, so lambda = -+ c alpha sqrt(gamma^dd), with c^2 = c_s^2 + v_A^2 - c_s^2 v_A^2
 // = (gamma p + b^2) / (w + b^2) for that state; with cleaning each axis's bound is
 // max(c, c_h) alpha sqrt(gamma^dd).  cfl_geo: sum_d alpha sqrt(gamma^dd) / dx_d (centre table).
+// The same for any state at rest (density rho, pressure p, b^2 = alpha^2 gamma_ij B^i B^j).
 template <bool CLEAN>
-__device__ __forceinline__ double atm_cfl_rate(const KParams& kp, double b2, double cfl_geo) {
-  const double gp = kp.gamma * kp.p_atm;
-  const double w = fma(kp.gfac, kp.p_atm, kp.rho_floor);
+__device__ __forceinline__ double rest_cfl_rate(const KParams& kp, double rho, double p, double b2,
+                                                double cfl_geo) {
+  const double gp = kp.gamma * p;
+  const double w = fma(kp.gfac, p, rho);
   const double c2 = (gp + b2) * rcp_fast(w + b2);
-  double c = c2 * rsqrt(c2);
+  double c = c2 > 0.0 ? c2 * rsqrt(c2) : 0.0;
   if (CLEAN) c = fmax(c, kp.ch);
   return c * cfl_geo;
+}
+template <bool CLEAN>
+__device__ __forceinline__ double atm_cfl_rate(const KParams& kp, double b2, double cfl_geo) {
+  return rest_cfl_rate<CLEAN>(kp, kp.rho_floor, kp.p_atm, b2, cfl_geo);
 }
 
 // Which warps of a TX x TY tile compute its extra faces on plane k: the top row of y faces (one
@@ -1373,6 +1379,16 @@ __global__ void __launch_bounds__(256) k_max_speed(const KParams kp, const typen
     for (int f = 0; f < 9; ++f) Pc[f] = (R)P[f * kp.fs + off];
     if (!CLEAN) Pc[8] = R(0);
     const Geom<R> G = make_geom<DIAG>(m);
+    if constexpr (DIAG && !MIXED) {
+      // a cell at rest (the atmosphere, most of a star's grid): the closed form
+      if (Pc[P_UX] == 0.0 && Pc[P_UY] == 0.0 && Pc[P_UZ] == 0.0) {
+        const double b2 = G.alp * G.alp *
+                          (G.gxx * Pc[P_BX] * Pc[P_BX] + G.gyy * Pc[P_BY] * Pc[P_BY] + G.gzz * Pc[P_BZ] * Pc[P_BZ]);
+        v = fmax(v, rest_cfl_rate<CLEAN>(kp, Pc[P_RHO], Pc[P_PRS], b2,
+                                         __ldg(kp.geo_c + GEO_N * kp.ms + met_off(kp, i, j, k))));
+        continue;
+      }
+    }
     v = fmax(v, cell_max_speed<YA, ZA, CLEAN, DIAG>(kp, G, Pc, c));
   }
   block_stats<256>(sc, v, 0, 0, true);
