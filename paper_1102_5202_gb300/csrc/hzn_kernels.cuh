@@ -733,7 +733,18 @@ __device__ __forceinline__ double cell_max_speed(const KParams& kp, const Geom<R
 // C = -c^2 gamma^dd, so lambda = -+ c alpha sqrt(gamma^dd), with c^2 = c_s^2 + v_A^2 - c_s^2 v_A^2
 // = (gamma p + b^2) / (w + b^2) for that state; with cleaning each axis's bound is
 // max(c, c_h) alpha sqrt(gamma^dd).  cfl_geo: sum_d alpha sqrt(gamma^dd) / dx_d (centre table).
-// The same for any state at rest (density rho, pressure p, b^2 = alpha^2 gamma_ij B^i B^j).
+template <bool CLEAN>
+__device__ __forceinline__ double atm_cfl_rate(const KParams& kp, double b2, double cfl_geo) {
+  const double gp = kp.gamma * kp.p_atm;
+  const double w = fma(kp.gfac, kp.p_atm, kp.rho_floor);
+  const double c2 = (gp + b2) * rcp_fast(w + b2);
+  double c = c2 * rsqrt(c2);
+  if (CLEAN) c = fmax(c, kp.ch);
+  return c * cfl_geo;
+}
+
+// The same for any state at rest (density rho, pressure p, b^2 = alpha^2 gamma_ij B^i B^j; a
+// state with c^2 = 0 has rate c_h, or 0 without cleaning).
 template <bool CLEAN>
 __device__ __forceinline__ double rest_cfl_rate(const KParams& kp, double rho, double p, double b2,
                                                 double cfl_geo) {
@@ -743,10 +754,6 @@ __device__ __forceinline__ double rest_cfl_rate(const KParams& kp, double rho, d
   double c = c2 > 0.0 ? c2 * rsqrt(c2) : 0.0;
   if (CLEAN) c = fmax(c, kp.ch);
   return c * cfl_geo;
-}
-template <bool CLEAN>
-__device__ __forceinline__ double atm_cfl_rate(const KParams& kp, double b2, double cfl_geo) {
-  return rest_cfl_rate<CLEAN>(kp, kp.rho_floor, kp.p_atm, b2, cfl_geo);
 }
 
 // Which warps of a TX x TY tile compute its extra faces on plane k: the top row of y faces (one
