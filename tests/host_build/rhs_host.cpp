@@ -70,7 +70,7 @@ void setup(Host& h, const int n[3], const double dx[3], const int bc[3], double 
               met[(((long long)f * mz + k) * my + j) * mx + i];
 
   // geometry tables of a DIAG metric over the table kernel's index range
-  h.gc.assign((size_t)(GEO_N * kp.ms), nan);
+  h.gc.assign((size_t)(GEO_C * kp.ms), nan);
   h.gf.assign((size_t)(3 * GEO_F * kp.ms), nan);
   h.gs.assign((size_t)(3 * GEO_S * kp.ms), nan);
   const double* M = h.M.data();
@@ -82,7 +82,13 @@ void setup(Host& h, const int n[3], const double dx[3], const int bc[3], double 
         if (cell) {
           double m[10];
           load_metric<true>(kp, M, mo, m);
-          geo_store(h.gc.data(), mo, kp.ms, make_geom<true>(m));
+          const Geom<double> Gc = make_geom<true>(m);
+          geo_store(h.gc.data(), mo, kp.ms, Gc);
+          // sum over active axes of alpha sqrt(gamma^dd) / dx_d, as the table kernel forms it
+          double r = Gc.alp * std::sqrt(Gc.ixx) * kp.idx;
+          if (kp.gy) r += Gc.alp * std::sqrt(Gc.iyy) * kp.idy;
+          if (kp.gz) r += Gc.alp * std::sqrt(Gc.izz) * kp.idz;
+          h.gc[GEO_N * kp.ms + mo] = r;
         }
         for (int d = 0; d < 3; ++d) {
           if ((d == 1 && !kp.gy) || (d == 2 && !kp.gz)) continue;
@@ -330,4 +336,32 @@ extern "C" double dev_max_speed(const int* n, const double* dx, const int* bc, d
   HZ_MS(true, true, 0, 0) HZ_MS(true, true, 0, 1) HZ_MS(true, true, 1, 0) HZ_MS(true, true, 1, 1)
 #undef HZ_MS
   return -1.0;
+}
+
+// The CFL rate of a grid whose cells are all at rest on a zero-shift diagonal metric, from the
+// closed form the kernels use for such cells (rest_cfl_rate); layouts as dev_rhs.
+extern "C" double dev_rest_max_speed(const int* n, const double* dx, const int* bc, double gamma,
+                                     int clean, double ch, const double* met, const double* prim) {
+  Host h;
+  setup(h, n, dx, bc, gamma, clean, ch, 0.0, met, prim);
+  const KParams& kp = h.kp;
+  double v = 0.0;
+  for (int k = 0; k < kp.nz; ++k)
+    for (int j = 0; j < kp.ny; ++j)
+      for (int i = 0; i < kp.nx; ++i) {
+        const long long off = (long long)k * kp.plane + (long long)j * kp.pitch + i;
+        const long long mo = met_off(kp, i, j, k);
+        double m[10];
+        load_metric<true>(kp, h.M.data(), mo, m);
+        const Geom<double> G = make_geom<true>(m);
+        double P[9];
+        for (int f = 0; f < 9; ++f) P[f] = h.P[f * kp.fs + off];
+        if (P[P_UX] != 0.0 || P[P_UY] != 0.0 || P[P_UZ] != 0.0) return -1.0;
+        const double b2 = G.alp * G.alp * (G.gxx * P[P_BX] * P[P_BX] + G.gyy * P[P_BY] * P[P_BY] +
+                                           G.gzz * P[P_BZ] * P[P_BZ]);
+        const double r = clean ? rest_cfl_rate<true>(kp, P[P_RHO], P[P_PRS], b2, h.gc[GEO_N * kp.ms + mo])
+                               : rest_cfl_rate<false>(kp, P[P_RHO], P[P_PRS], b2, h.gc[GEO_N * kp.ms + mo]);
+        v = std::fmax(v, r);
+      }
+  return v;
 }

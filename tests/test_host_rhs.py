@@ -47,6 +47,8 @@ def dev():
     L.dev_recover.restype = None
     L.dev_max_speed.argtypes = [ip, dp, ip, cd, ci, cd, ci, dp, dp]
     L.dev_max_speed.restype = cd
+    L.dev_rest_max_speed.argtypes = [ip, dp, ip, cd, ci, cd, dp, dp]
+    L.dev_rest_max_speed.restype = cd
     return L
 
 
@@ -192,3 +194,32 @@ def test_cfl_maximum_matches_oracle(dev, case, clean):
     want = O.max_speed(O.make_grid(P.n, P.dx, P.bc), O.make_opts(P.gamma, cleaning=bool(clean), ch=P.ch),
                        met, prim)
     assert got == pytest.approx(want, rel=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("clean", [0, 1])
+def test_rest_state_cfl_rate_closed_form(dev, clean, seed):
+    """The closed-form CFL rate the kernels take for cells at rest on a zero-shift diagonal
+    metric (rest_cfl_rate: lambda = -+ c alpha sqrt(gamma^dd) with c^2 = (Gamma p + b^2)/(w + b^2),
+    b^2 = alpha^2 gamma_ij B^i B^j, widened to the cleaning speed) against the oracle's general
+    dispersion-relation roots, on the capped-Schwarzschild blob metric with random densities,
+    pressures and fields spanning six decades, magnetically and thermally dominated cells both
+    (the grid maximum is one cell's rate; each seed selects another cell)."""
+    P = W.blob3d(12)
+    rng = np.random.Generator(np.random.PCG64(17 + seed))
+    shape = P.prim.shape[1:]
+    prim = np.zeros_like(P.prim)
+    prim[0] = 10.0 ** rng.uniform(-6, 0, shape)
+    prim[1] = 10.0 ** rng.uniform(-8, 0, shape)
+    prim[5:8] = rng.uniform(-1, 1, (3,) + shape) * 10.0 ** rng.uniform(-4, 0, shape)
+    ch = 0.3
+    n = (ctypes.c_int * 3)(*P.n)
+    dx = (ctypes.c_double * 3)(*P.dx)
+    bc = (ctypes.c_int * 3)(*P.bc)
+    met = np.ascontiguousarray(P.metric, dtype=np.float64)
+    prim = np.ascontiguousarray(prim)
+    dp = ctypes.POINTER(ctypes.c_double)
+    got = dev.dev_rest_max_speed(n, dx, bc, P.gamma, clean, ch, met.ctypes.data_as(dp), prim.ctypes.data_as(dp))
+    want = O.max_speed(O.make_grid(P.n, P.dx, P.bc), O.make_opts(P.gamma, cleaning=bool(clean), ch=ch), met, prim)
+    assert got > 0.0
+    assert got == pytest.approx(want, rel=1e-13)
