@@ -99,6 +99,9 @@ def parse():
                     help="skip the mixed error statement (100 FP64 and 100 mixed steps at the mixed size, about a minute)")
     ap.add_argument("--ensemble-tubes", type=int, default=512)
     ap.add_argument("--n-mixed", type=int, default=384, help="cells per axis of the mixed line")
+    ap.add_argument("--sweep", default="",
+                    help="comma-separated cells per axis: instead of the benchmark line, print one JSON line "
+                         "of FP64 and mixed ZU/s of the blob at each size (cost per zone update against grid size)")
     return ap.parse_args()
 
 
@@ -785,11 +788,49 @@ def run_reference(args, rank, world):
     return line
 
 
+def run_sweep(args):
+    """Zone updates per second of the blob against its size, FP64 and mixed: each size `warmup`
+    untimed CFL steps, then `steps` steps timed with CUDA events on the solver's stream."""
+    import torch
+
+    from paper_1102_5202_gb300 import hzn
+    from paper_1102_5202_gb300 import workloads as W
+
+    rows = []
+    for n in (int(x) for x in args.sweep.split(",") if x):
+        P = W.blob3d(n)
+        row = {"n": n, "cells": P.ncell}
+        for name, prec in (("fp64", hzn.HZ_FP64), ("mixed", hzn.HZ_MIXED)):
+            s = hzn.Solver.for_problem(P, precision=prec)
+            for _ in range(args.warmup):
+                s.step_cfl(0.5, 1e30)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(s.stream):
+                a.record(s.stream)
+                for _ in range(args.steps):
+                    s.step_cfl(0.5, 1e30)
+                b.record(s.stream)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) * 1e-3
+            row[name] = P.ncell * args.steps / sec
+            row[name + "_ms_per_step"] = sec / args.steps * 1e3
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+        rows.append(row)
+    print(json.dumps({"sweep": "blob3d", "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "rows": rows}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     run_gpu(args, rank, world, local)
 

@@ -1410,8 +1410,7 @@ inline int blocks_for(long long n, int threads) {
 
 // One substep launch.  FP64 kernels run on a persistent grid: as many blocks as are resident at
 // once (blocks per SM from the occupancy calculator, once per instantiation, times the SMs),
-// each taking an equal share of the plane-tiles, but at least 8 plane-tiles per block in 3-D
-// and one tile in 1-D and 2-D.  Mixed
+// each taking an equal share of the plane-tiles, at least one.  Mixed
 // and double-word kernels: one block per tile column and z chunk.  dyn: the dynamic shared
 // memory (the z-face carry of the MC kernels).
 template <int TX, int TY, bool YA, bool ZA, bool CLEAN, bool DIAG, bool MIXED, int RECON, bool PAIR>
@@ -1438,11 +1437,10 @@ void launch_substep_one(const KParams& kp, const StageArgs& sa, const typename P
   }
   const long long total = (long long)((kp.nx + TX - 1) / TX) * ((kp.ny + TY - 1) / TY) * kp.nz;
   long long g = (long long)per_sm * (kp.nsm > 0 ? kp.nsm : 1);
-  // 3-D: at least 8 plane-tiles per block (a z segment's first face costs a full stencil);
-  // 1-D and 2-D (one plane): at least one tile per block, so that a small grid spreads over
-  // as many SMs as it has tiles
-  const long long cap = ZA ? (total + 7) / 8 : total;
-  if (g > cap) g = cap;
+  // at least one plane-tile per block: a grid with fewer plane-tiles than resident blocks
+  // spreads over as many blocks as it has plane-tiles (in 3-D a z segment's first face then
+  // costs a full stencil more per plane, which is cheaper than marching 8 planes in series)
+  if (g > total) g = total;
   if (g < 1) g = 1;
   kern<<<(unsigned)g, TX * TY, dyn, st>>>(kp, sa, M, sc);
 }
