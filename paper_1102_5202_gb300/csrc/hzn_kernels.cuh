@@ -1032,9 +1032,7 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
   const int i = i0 + tx, j = j0 + ty;
   const bool own = i < kp.nx && j < kp.ny;
 
-#ifdef __CUDACC__
   if constexpr (STAGE) stage_plane<TX, TY, NV>(kp, P, sp, i0, j0, kz0);
-#endif
   if constexpr (!PAIR) {
     if (ZA && own) {
       if constexpr (ZCARRY)
@@ -1178,11 +1176,9 @@ k_substep(const KParams kp, const StageArgs sa, const typename Prec<MIXED>::S* _
       }
     }
     __syncthreads();
-#ifdef __CUDACC__
     if constexpr (STAGE) {
       if (k + 1 < kz1) stage_plane<TX, TY, NV>(kp, P, sp, i0, j0, k + 1);
     }
-#endif
 
     // ---- cell update of plane k
     if (own) {
